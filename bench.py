@@ -1,0 +1,500 @@
+"""Benchmark of the fused entropic lattice-BGK step on GB300.
+
+Default workload (1 GPU): D3Q27, 512^3 periodic Taylor-Green vortex (u0 = 0.1, rho0 = 1,
+Re = 1600 with nu = u0 (N / 2 pi) / Re), entropic equilibrium, populations stored as
+binary16 f - w rho0 with FP32 collision, fused diagnostics every 10 steps.  One bench
+step is one lattice time step of the whole grid.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload tgv3d|shear2d|tgv2d|batch]
+                  [--precision f16s|f32|f64] [--impl reference]
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload
+(rank 0 only).  Under torchrun (N > 1) every rank runs an independent replica of the
+workload on its own GPU (no data-path collective); the barrier and the max over ranks
+bound the timed region.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GLUPS and % of HBM roofline; FP16-store vs FP32/FP64 at stated L2 velocity error"
+PREC = {"f64": 0, "f32": 1, "f16s": 2}
+ESIZE = {0: 8, 1: 4, 2: 2}
+PREC_NAME = {0: "F64", 1: "F32", 2: "F16S"}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--workload", default="tgv3d", choices=["tgv3d", "shear2d", "tgv2d", "batch"])
+    p.add_argument("--precision", default=None, choices=list(PREC))
+    p.add_argument("--bulk", type=int, default=0)
+    p.add_argument("--eq", default="entropic", choices=["entropic", "poly2", "product"])
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--n", type=int, default=None, help="lattice side (default: the workload's)")
+    p.add_argument("--diag-every", type=int, default=10)
+    p.add_argument("--no-extras", action="store_true", help="skip the comparison runs")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- workloads
+
+def workload(args):
+    """Workload description: lattice, dims, tau, precision, field recipe."""
+    eq = {"entropic": 0, "poly2": 1, "product": 2}[args.eq]
+    if args.workload == "tgv3d":
+        n = args.n or 512
+        u0 = 0.1
+        nu = u0 * (n / (2 * math.pi)) / 1600.0
+        prec = PREC[args.precision or "f16s"]
+        return dict(name=f"D3Q27 {n}^3 periodic Taylor-Green vortex (u0=0.1, rho0=1, Re=1600)",
+                    D=3, dims=(n, n, n), tau=0.5 + 3 * nu, prec=prec, eq=eq, u0=u0)
+    if args.workload == "shear2d":
+        n = args.n or 4096
+        prec = PREC[args.precision or "f32"]
+        return dict(name=f"D2Q9 {n}^2 periodic double shear layer (u0=0.1, kappa=80, delta=0.05)",
+                    D=2, dims=(n, n, 1), tau=0.5 + 3e-5, prec=prec, eq=eq, u0=0.1)
+    if args.workload == "tgv2d":
+        n = args.n or 64
+        prec = PREC[args.precision or "f64"]
+        return dict(name=f"D2Q9 {n}^2 periodic Taylor-Green vortex (u0=0.05, tau=0.8)",
+                    D=2, dims=(n, n, 1), tau=0.8, prec=prec, eq=eq, u0=0.05)
+    return dict(name="4096 independent D2Q9 periodic lattices, sides log-uniform in [16,256], "
+                     "one shear or acoustic wave each (amplitude 1e-4), FP64",
+                D=2, dims=None, tau=None, prec=0, eq=eq, u0=0.3)
+
+
+def fields_device(w, torch, dev):
+    """Initial fields as float32 device tensors (flat rho, u[D][ncell])."""
+    D, (nx, ny, nz) = w["D"], w["dims"]
+    if w["name"].startswith("D3Q27"):
+        n = nx
+        t = torch.arange(n, device=dev, dtype=torch.float64) * (2 * math.pi / n)
+        s, c, c2 = torch.sin(t), torch.cos(t), torch.cos(2 * t)
+        u0 = w["u0"]
+        ux = u0 * c[:, None, None] * c[None, :, None] * s[None, None, :]
+        uy = -u0 * c[:, None, None] * s[None, :, None] * c[None, None, :]
+        rho = 1.0 + u0 * u0 * 3.0 / 16.0 * (c2[None, :, None] + c2[None, None, :]) * (c2[:, None, None] + 2.0)
+        u = torch.stack([ux.reshape(-1), uy.reshape(-1), torch.zeros_like(ux).reshape(-1)])
+        return rho.reshape(-1).float().contiguous(), u.float().contiguous()
+    from paper_2303_08163_gb300 import inputs
+    if "shear" in w["name"]:
+        rho, u = inputs.double_shear_layer(nx, dtype=np.float32)
+    else:
+        rho, u = inputs.taylor_green_2d(nx, u0=w["u0"])
+    return (torch.from_numpy(np.ascontiguousarray(rho, dtype=np.float32)).to(dev),
+            torch.from_numpy(np.ascontiguousarray(u, dtype=np.float32)).to(dev))
+
+
+# ------------------------------------------------------------------------------- helpers
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
+        load = [v for v, r in zip(sm, rows) if float(r[3]) > 200.0] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def source_hash():
+    """Hash of the step-kernel sources, to match committed ncu traffic to the code."""
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2303_08163_gb300", "csrc")
+    for name in ("k_tma.cuh", "lbm_device.cuh", "lbm_common.cuh", "ptx.cuh", "k_generic_step.cuh"):
+        h.update(open(os.path.join(d, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload_name, ncell):
+    """DRAM bytes per launch from the committed ncu summary, scaled to ncell; None when the
+    kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        recs = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    for r in recs:
+        if r.get("kernel") == kernel and r.get("workload") == workload_name and r.get("source_hash") == source_hash():
+            return r["dram_bytes_per_cell"] * ncell
+    return None
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
+
+
+# ----------------------------------------------------------------------- CPU baseline leg
+
+def oracle_sample(w, seconds):
+    """Time the FP64 CPU oracle (single thread, as it stands) on a bounded sample of the
+    workload; returns (GLUPS, description)."""
+    from oracle import core
+    from paper_2303_08163_gb300 import inputs
+    D = w["D"]
+    if w["dims"] is None:
+        n = 64
+        dims = (n, n, 1)
+        table = {"nx": [n], "ny": [n], "nmode": [2], "U0": [0.1], "tau": [0.8], "kind": [1], "amp": 1e-4}
+        rho, u = inputs.linear_mode_fields(table, 0)
+        tau = 0.8
+    elif D == 3:
+        n = 48
+        dims = (n, n, n)
+        rho, u = inputs.taylor_green_3d(n, u0=w["u0"])
+        tau = w["tau"]
+    else:
+        n = 256
+        dims = (n, n, 1)
+        rho, u = inputs.taylor_green_2d(n, u0=0.05)
+        tau = w["tau"]
+    f = core.init(D, dims, w["eq"], rho, u)
+    t0 = time.perf_counter()
+    f = core.step(D, dims, w["eq"], 0, tau, 1, f)
+    one = time.perf_counter() - t0
+    steps = max(1, int(seconds / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    core.step(D, dims, w["eq"], 0, tau, steps, f)
+    dt = time.perf_counter() - t0
+    ncell = int(np.prod(dims))
+    return ncell * steps / dt / 1e9, (f"FP64 CPU oracle, single thread, D{D}Q{3 ** D} "
+                                      f"{'x'.join(str(d) for d in dims if d > 1)} sample of the workload, "
+                                      f"{steps} steps in {dt:.1f} s")
+
+
+def run_reference(args):
+    rank, _, ws = dist_env()
+    if rank != 0:
+        return
+    w = workload(args)
+    from oracle import core
+    from paper_2303_08163_gb300 import inputs
+    D = w["D"]
+    dims = (32, 32, 32) if D == 3 else (128, 128, 1)
+    if w["dims"] is None:
+        dims = (64, 64, 1)
+    ncell = int(np.prod(dims))
+    rho, u = inputs.random_state(D, dims, seed=5, rho_range=(0.99, 1.01), u_max=0.05)
+    f = core.init(D, dims, w["eq"], rho, u)
+    tau = w["tau"] or 0.8
+    for _ in range(args.warmup):
+        f = core.step(D, dims, w["eq"], args.bulk, tau, 1, f)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = core.step(D, dims, w["eq"], args.bulk, tau, 1, f)
+    dt = time.perf_counter() - t0
+    glups = ncell * args.steps / dt / 1e9
+    sample = (f"each step: one FP64 CPU-oracle step of a {'x'.join(str(d) for d in dims if d > 1)} "
+              f"sample lattice of the workload (single thread)")
+    line = {"impl": "reference", "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w["name"], "sample": sample},
+            "cpu_baseline": {"value": glups, "unit": "GLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": glups, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------- native arm
+
+def timed_steps(torch, lat, steps, diag_every, stream):
+    """Run `steps` steps with an event pair around each; returns (total ms, per-step ms,
+    indices of steps that carried fused diagnostics)."""
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    t_first = lat.step_count
+    evs[0].record(stream)
+    for s in range(steps):
+        lat.step(1)
+        evs[s + 1].record(stream)
+    evs[-1].synchronize()
+    per = [evs[s].elapsed_time(evs[s + 1]) for s in range(steps)]
+    diag_steps = [s for s in range(steps) if diag_every > 0 and (t_first + s) % diag_every == 0]
+    return evs[0].elapsed_time(evs[-1]), per, diag_steps
+
+
+def velocity_error(torch, lbm, dev, n=128):
+    """Relative L2 velocity error of the F32 and F16S paths against the FP64 path on the
+    D3Q27 n^3 Taylor-Green vortex (Re = 1600) after four convective times."""
+    u0 = 0.1
+    nu = u0 * (n / (2 * math.pi)) / 1600.0
+    tau = 0.5 + 3 * nu
+    steps = int(round(4 * n / (2 * math.pi * u0)))
+    w = dict(name="D3Q27", D=3, dims=(n, n, n), u0=u0)
+    rho, u = fields_device(w, torch, dev)
+    out = {}
+    us = {}
+    for prec in (0, 1, 2):
+        lat = lbm.Lattice(lbm.D3Q27, (n, n, n), tau, 0, 0, prec)
+        lat.init_fields(rho, u, dtype=np.float32)
+        lat.step(steps)
+        r = torch.empty(n ** 3, device=dev, dtype=torch.float64)
+        v = torch.empty(3, n ** 3, device=dev, dtype=torch.float64)
+        lat.moments(dtype=np.float64, out=(r, v))
+        us[prec] = v
+        lat.close()
+    for prec in (1, 2):
+        out[PREC_NAME[prec]] = float(torch.linalg.norm(us[prec] - us[0]) / torch.linalg.norm(us[0]))
+    out["case"] = f"D3Q27 {n}^3 Taylor-Green, Re=1600, {steps} steps (4 convective times)"
+    out["reference"] = "FP64 GPU path (equal to the CPU oracle to 1e-12 in the parity tests)"
+    return out
+
+
+def run_native(args):
+    import torch
+    from paper_2303_08163_gb300 import lbm
+
+    rank, local, ws = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lbm.load()
+    stream = torch.cuda.current_stream()
+    w = workload(args)
+    if w["dims"] is None:
+        return run_batch(args, w, torch, lbm, dev, rank, ws)
+    D, dims, prec = w["D"], w["dims"], w["prec"]
+    Q = 3 ** D
+    ncell = int(np.prod(dims))
+    lat = lbm.Lattice(lbm.D3Q27 if D == 3 else lbm.D2Q9, dims, w["tau"], w["eq"], args.bulk, prec)
+    rho, u = fields_device(w, torch, dev)
+    lat.init_fields(rho, u, dtype=np.float32)
+    lat.set_option(lbm.OPT_TUNE, 1)
+    lat.set_option(lbm.OPT_DIAG_EVERY, args.diag_every)
+    lat.init_fields(rho, u, dtype=np.float32)
+    for _ in range(args.warmup):
+        lat.step(1)
+    torch.cuda.synchronize()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        total_ms, per, diag_steps = timed_steps(torch, lat, args.steps, args.diag_every, stream)
+    torch.cuda.synchronize()
+    clocks = clk.summary()
+    t_max = total_ms
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        dist.barrier()
+    hist = lat.diag_history()
+    plain = [per[s] for s in range(len(per)) if s not in set(diag_steps)] or per
+    launch_ms = statistics.mean(plain)
+    algo_bytes = 2 * Q * ESIZE[prec] * ncell
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    achieved = algo_bytes / (launch_ms * 1e-3) / 1e9
+    info = lat.launch_info()
+    kname = "k_step_tma" if info["kernel"] == 2 else "k_step_generic"
+    traffic = ncu_traffic(kname, w["name"], ncell)
+    glups = ws * ncell * args.steps / (t_max * 1e-3) / 1e9
+    # end to end through the C ABI with pinned host buffers
+    rho_h = rho.cpu().pin_memory()
+    u_h = u.cpu().pin_memory()
+    rout = torch.empty(ncell, dtype=torch.float32).pin_memory()
+    uout = torch.empty(D, ncell, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.init_fields(rho_h, u_h, dtype=np.float32)
+    lat.step(args.steps)
+    lat.moments(dtype=np.float32, out=(rout, uout))
+    e1.record(stream)
+    e1.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": ws * ncell * args.steps / (e2e_ms * 1e-3) / 1e9, "unit": "GLUPS",
+           "h2d_bytes_per_step": (rho_h.numel() + u_h.numel()) * 4 / args.steps,
+           "d2h_bytes_per_step": (rout.numel() + uout.numel()) * 4 / args.steps,
+           "path": "lbm_init_fields(host) + lbm_step(K) + lbm_moments(host), pinned buffers"}
+    launches = args.steps + len(diag_steps)
+    extras = {}
+    if not args.no_extras and rank == 0:
+        lat.close()
+        del lat
+        torch.cuda.empty_cache()
+        extras["precision_compare"] = compare_precisions(torch, lbm, dev, w, args, rho, u)
+        if w["D"] == 3:
+            extras["l2_velocity_error"] = velocity_error(torch, lbm, dev)
+    cpu = None
+    if rank == 0:
+        g, desc = oracle_sample(w, args.cpu_seconds)
+        cpu = {"value": g, "unit": "GLUPS", "cores": 1, "kind": "oracle", "sample": desc}
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32",
+        "storage": PREC_NAME[prec], "data": "synthetic",
+        "config": {"workload": w["name"], "lattice": f"D{D}Q{Q}", "dims": list(dims), "tau": w["tau"],
+                   "equilibrium": args.eq, "bulk_corr": args.bulk, "precision": PREC_NAME[prec],
+                   "diag_every": args.diag_every, "state_bytes": info["storage_bytes"],
+                   "l2": "inputs larger than L2 (the population array is re-read every step)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU", "launch": info},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                     "kernel": kname, "algorithmic_bytes_per_launch": algo_bytes,
+                     "avg_launch_ms": launch_ms},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        "diag_last": {k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in hist[-1].items()} if hist else None,
+    }
+    line.update(extras)
+    print(json.dumps(line), flush=True)
+
+
+def compare_precisions(torch, lbm, dev, w, args, rho, u):
+    """Device-timed GLUPS of the same workload in the other storage precisions."""
+    out = {}
+    D, dims = w["D"], w["dims"]
+    ncell = int(np.prod(dims))
+    Q = 3 ** D
+    for prec in (2, 1, 0):
+        for bulk in (0, 1):
+            key = PREC_NAME[prec] + ("+bulk" if bulk else "")
+            try:
+                lat = lbm.Lattice(lbm.D3Q27 if D == 3 else lbm.D2Q9, dims, w["tau"], w["eq"], bulk, prec)
+            except lbm.LBMError as e:
+                out[key] = {"error": str(e)}
+                continue
+            lat.init_fields(rho, u, dtype=np.float32)
+            lat.set_option(lbm.OPT_TUNE, 1)
+            lat.init_fields(rho, u, dtype=np.float32)
+            steps = 40 if prec != 0 else 10
+            lat.step(4)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            lat.step(steps)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            gb = 2 * Q * ESIZE[prec] * ncell / (ms * 1e-3) / 1e9
+            out[key] = {"GLUPS": ncell / (ms * 1e-3) / 1e9, "ms_per_step": ms, "GB_s": gb,
+                        "launch": lat.launch_info()}
+            lat.close()
+            torch.cuda.empty_cache()
+    return out
+
+
+def run_batch(args, w, torch, lbm, dev, rank, ws):
+    from paper_2303_08163_gb300 import inputs
+    table = inputs.linear_mode_batch(count=4096, seed=2303)
+    count = len(table["nx"])
+    dims = np.stack([table["nx"], table["ny"], np.ones(count, dtype=np.int32)], axis=1)
+    fields = [inputs.linear_mode_fields(table, k) for k in range(count)]
+    rho = np.concatenate([f[0] for f in fields])
+    u = np.concatenate([f[1].reshape(-1) for f in fields])
+    kvec = np.stack([table["nmode"], np.zeros(count, np.int32), np.zeros(count, np.int32)], axis=1)
+    b = lbm.Batch(lbm.D2Q9, dims, table["tau"], w["eq"], args.bulk)
+    b.init_fields(rho, u)
+    b.set_probe(kvec, 10)
+    total = int(b.cell_start[-1])
+    b.step(args.warmup)
+    b.sync()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0.record(stream)
+        b.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    glups = total * args.steps / (ms * 1e-3) / 1e9
+    algo = 2 * 9 * 8 * total * args.steps
+    peak = measured_peaks().get("hbm_gbs") or 6800.0
+    g, desc = oracle_sample(w, args.cpu_seconds)
+    line = {"metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "total_cells": total, "probe_every": 10,
+                       "launch": b.launch_info()},
+            "roofline": {"bound": "hbm", "achieved": algo / (ms * 1e-3) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": algo / (ms * 1e-3) / 1e9 / peak, "traffic": None,
+                         "note": "FP64 collision: bound by the FP64 pipe, not by HBM"},
+            "cpu_baseline": {"value": g, "unit": "GLUPS", "cores": 1, "kind": "oracle", "sample": desc},
+            "gpu_launches": 1, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -30,7 +30,8 @@
  * Storage: populations live in device memory owned by the library, as shifted values
  *   f_i - w_i rho0 in FP64, FP32 or IEEE binary16 (round-to-nearest-even); the collision
  *   runs in FP64 for FP64 storage and in FP32 otherwise.
- * dtype arguments: LBM_DT_F64 (double) or LBM_DT_F32 (float) for caller buffers.
+ * dtype arguments: LBM_DT_F64 (double) or LBM_DT_F32 (float) for caller buffers;
+ *   population calls also take LBM_DT_STORAGE (exact checkpoint of the stored values).
  * on_device: 0 = caller pointer is host memory (pageable or pinned), 1 = device memory
  *   on the context's device.
  * Ownership: the library owns its objects and all device memory it allocates; caller
@@ -69,7 +70,12 @@ enum lbm_precision {
     LBM_F16S = 2 /* binary16 storage of f - w rho0 (RN-even), FP32 collision */
 };
 
-enum lbm_dtype { LBM_DT_F64 = 0, LBM_DT_F32 = 1 };
+enum lbm_dtype {
+    LBM_DT_F64 = 0,    /* double */
+    LBM_DT_F32 = 1,    /* float */
+    LBM_DT_STORAGE = 2 /* populations only: the stored shifted values f - w rho0 in the
+                          storage type (double, float or binary16), bit for bit */
+};
 
 enum lbm_status {
     LBM_OK = 0,
@@ -149,14 +155,18 @@ int lbm_diagnostics(lbm_ctx *ctx, lbm_diag *out);
  */
 int lbm_diag_history(lbm_ctx *ctx, lbm_diag *out, int64_t max, int64_t *count);
 
-/* Canonical populations f[Q][ncell] (not shifted) of the current state, in dtype. */
+/* Canonical populations f[Q][ncell] of the current state: not shifted for LBM_DT_F64 and
+ * LBM_DT_F32, the stored shifted values for LBM_DT_STORAGE. */
 int lbm_get_populations(lbm_ctx *ctx, void *f, int dtype, int on_device);
 
-/* Replace the current state with canonical populations f[Q][ncell] (not shifted); the
- * step counter is kept, so a checkpoint is (lbm_get_populations, lbm_step_count). */
+/* Replace the current state with canonical populations f[Q][ncell] (same dtype meaning
+ * as lbm_get_populations); the step counter is kept.  A checkpoint that resumes bit for
+ * bit is (lbm_get_populations(LBM_DT_STORAGE), lbm_step_count). */
 int lbm_set_populations(lbm_ctx *ctx, const void *f, int dtype, int on_device);
 
-/* Set the step counter (after lbm_set_populations when resuming a checkpoint). */
+/* Set the step counter t.  The stored layout depends on the parity of t, so a change of
+ * parity moves the current state into the new layout (the state is unchanged).  To resume a
+ * checkpoint: lbm_set_step_count(t), then lbm_set_populations(f). */
 int lbm_set_step_count(lbm_ctx *ctx, int64_t step);
 
 /*
@@ -176,6 +186,18 @@ int lbm_step_count(lbm_ctx *ctx, int64_t *out);
  * shared memory bytes, out[7] = population storage bytes.
  */
 int lbm_launch_info(lbm_ctx *ctx, int64_t out[8]);
+
+/*
+ * Choose the step kernel's launch shape explicitly.  shape = {kernel, threads, stages,
+ * rows, seg, cap}: kernel 1 = generic (threads per block, the rest ignored), 2 = TMA
+ * row-staged with `threads` colliding threads per block (a multiple of 32, at most 256;
+ * one copy-issuing warp is added), `stages` shared-memory stages (2..8), `rows`
+ * rows per job when whole rows fit, `seg` cells per row segment (seg >= Nx for whole
+ * rows; otherwise a multiple of 16 / sizeof(storage)) and `cap` bytes per direction
+ * buffer (1024, 2048, 4096 or 8192).  The block count is the largest that fits on the
+ * device.  Returns LBM_EINVAL for a shape the lattice or the device cannot run.
+ */
+int lbm_set_launch_shape(lbm_ctx *ctx, const int64_t shape[6]);
 
 /* Wait for all work of the object's stream; returns a sticky error if one occurred. */
 int lbm_sync(lbm_ctx *ctx);
@@ -204,8 +226,9 @@ int lbm_batch_init_fields(lbm_batch *b, const void *rho, const void *u, int dtyp
 
 /*
  * Record, at every step t with t % every_k == 0 (t counted from the last init), the
- * Fourier projections sum_r q(r) exp(-i k.r) of q = rho, j_x, j_y (FP64) for the
- * per-instance wave vector k = 2 pi (kvec[k][0] / Nx, kvec[k][1] / Ny, kvec[k][2] / Nz).
+ * Fourier projections sum_r q(r) exp(-i k.r) of q = rho, j_x, j_y, j_z (FP64, j = rho u)
+ * of the state at t, for the per-instance wave vector
+ * k = 2 pi (kvec[k][0] / Nx, kvec[k][1] / Ny, kvec[k][2] / Nz).
  * kvec: host int32 [count][3].  every_k >= 1.
  */
 int lbm_batch_set_probe(lbm_batch *b, const int32_t *kvec, int64_t every_k);
@@ -215,8 +238,8 @@ int lbm_batch_set_probe(lbm_batch *b, const int32_t *kvec, int64_t every_k);
 int lbm_batch_step(lbm_batch *b, int64_t n);
 
 /*
- * Copy the probe series to host: out[count][max_samples][3][2] (re, im of rho, j_x, j_y);
- * *nsamples receives the number of samples recorded so far (synchronises).  Pass
+ * Copy the probe series to host: out[count][max_samples][4][2] (re, im of rho, j_x, j_y,
+ * j_z); *nsamples receives the number of samples recorded so far (synchronises).  Pass
  * out = NULL to query *nsamples only.
  */
 int lbm_batch_probe_series(lbm_batch *b, double *out, int64_t max_samples, int64_t *nsamples);

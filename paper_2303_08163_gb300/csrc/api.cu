@@ -1,0 +1,1243 @@
+// api.cu -- the C ABI declared in include/lbm.h: object lifetimes, argument checks,
+// launch selection and the launch-shape autotuner.  All compute runs in the kernels of
+// k_generic*.cu, k_tma*.cu and k_batch.cu; this file only marshals arguments and orders
+// launches on the object's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <queue>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+using namespace lbmh;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int esize_of(int P) { return P == LBM_F64 ? 8 : (P == LBM_F32 ? 4 : 2); }
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 1;
+        }
+    }
+    return n;
+}
+
+int64_t wait_timeout_ns() {
+    const char *e = getenv("LBM_WAIT_TIMEOUT_NS");
+    if (e && *e) {
+        const long long v = atoll(e);
+        if (v > 0) return v;
+    }
+    return 2000000000LL;  // 2 s
+}
+
+constexpr int64_t kHistCap = 65536;
+constexpr int kPartialsCap = 152 * 32;
+
+}  // namespace
+
+struct lbm_ctx {
+    int lattice = 0, D = 2, Q = 9, eq = 0, bulk = 0, prec = 0;
+    int64_t dims[3] = {1, 1, 1};
+    int64_t ncell = 0;
+    double tau = 1, rho0 = 1, omega0 = 1, six_nu = 1;
+    cudaStream_t stream = nullptr;
+    Lattice lat{};
+    int64_t step = 0;
+    int sticky = 0;
+    // diagnostics
+    int64_t diag_every = 0;
+    double *partials = nullptr;  // [kPartialsCap][8]
+    double *hist = nullptr;      // [kHistCap][8]
+    double *scratch = nullptr;   // one record
+    int32_t *status = nullptr;
+    int64_t hist_count = 0;
+    // launch
+    int kernel_opt = 0;  // 0 auto, 1 generic, 2 tma
+    int kernel = 1;
+    int gen_threads = 256, gen_blocks = 1;
+    TmaShape tma{};
+    bool use_graph = false;
+    cudaGraphExec_t graph2 = nullptr;  // even + odd step
+    // grow-only device staging for calls with host buffers
+    void *stage[2] = {nullptr, nullptr};
+    size_t stage_cap[2] = {0, 0};
+};
+
+struct lbm_batch {
+    int lattice = 0, D = 2, Q = 9, eq = 0, bulk = 0;
+    int64_t count = 0, total = 0;
+    double rho0 = 1;
+    cudaStream_t stream = nullptr;
+    double *arena = nullptr;
+    int64_t *d_cell_start = nullptr;
+    int32_t *d_dims = nullptr;
+    double *d_omega = nullptr, *d_sixnu = nullptr;
+    int32_t *d_order = nullptr, *d_block_start = nullptr;
+    double2 *d_tw = nullptr;
+    int64_t *d_tw_off = nullptr;
+    double *d_series = nullptr;
+    int64_t max_samples = 0;
+    int32_t *d_status = nullptr;
+    int64_t every_k = 0;
+    int64_t step = 0;
+    int blocks = 0, threads = 256;
+    int64_t max_load = 0, mean_load = 0;
+    std::vector<int32_t> dims;
+    std::vector<int64_t> cell_start;
+    int sticky = 0;
+};
+
+namespace {
+
+int cuda_fail(const char *what, cudaError_t e) {
+    return fail(LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                      \
+    do {                                                    \
+        cudaError_t _e = (call);                            \
+        if (_e != cudaSuccess) return cuda_fail(what, _e);  \
+    } while (0)
+
+int ctx_check(lbm_ctx *c) {
+    if (!c) return fail(LBM_EINVAL, "null context");
+    if (c->sticky) return fail(LBM_ESTATE, "context is in an error state (%d); destroy it", c->sticky);
+    return LBM_OK;
+}
+
+int ctx_sticky(lbm_ctx *c, int code) {
+    if (code == LBM_ECUDA || code == LBM_ETIMEOUT || code == LBM_ENOMEM) c->sticky = code;
+    return code;
+}
+
+// Device status word: LBM_ETIMEOUT if a kernel's bounded wait ran out.
+int read_status(lbm_ctx *c) {
+    int32_t st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, c->status, sizeof st, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return ctx_sticky(c, cuda_fail("status read", e));
+    if (st != 0) return ctx_sticky(c, fail(LBM_ETIMEOUT, "a bounded device wait ran out (status %d)", st));
+    return LBM_OK;
+}
+
+StepArgs step_args(lbm_ctx *c, int odd, int diag) {
+    StepArgs a;
+    a.lat = c->lat;
+    a.eq = c->eq;
+    a.bulk = c->bulk;
+    a.rho0 = c->rho0;
+    a.omega0 = c->omega0;
+    a.six_nu = c->six_nu;
+    a.odd = odd;
+    a.diag = diag;
+    a.partials = c->partials;
+    a.status = c->status;
+    a.timeout_ns = wait_timeout_ns();
+    return a;
+}
+
+int launch_blocks(lbm_ctx *c) { return c->kernel == 2 ? c->tma.blocks : c->gen_blocks; }
+
+cudaError_t launch_one(lbm_ctx *c, int odd, int diag, cudaStream_t s) {
+    const StepArgs a = step_args(c, odd, diag);
+    if (c->kernel == 2) return step_tma(a, c->tma, s);
+    return step_generic(a, c->gen_blocks, c->gen_threads, s);
+}
+
+// Default TMA shape: whole rows (several per job when short) if a row fits a direction
+// buffer, else aligned segments; stage count from the shared-memory budget.
+bool default_tma_shape(lbm_ctx *c, TmaShape &t) {
+    const int es = esize_of(c->prec);
+    const int64_t rowb = c->lat.nx * (int64_t)es;
+    const int U = 16 / es;
+    t.threads = 256;
+    const int capmax = c->D == 3 ? 2048 : 8192;
+    int cap = 1024;
+    while (cap < rowb && cap < capmax) cap *= 2;
+    t.cap = cap;
+    if (rowb <= cap) {
+        t.seg = c->lat.nx;
+        t.rows = (int)std::max<int64_t>(1, std::min<int64_t>(cap / rowb, c->lat.ny));
+    } else {
+        t.seg = (cap / es - 2 * U) / U * U;
+        t.rows = 1;
+    }
+    const int stage = c->Q * cap;
+    t.stages = std::max(2, std::min(kTmaMaxStages, (110 * 1024) / stage));
+    t.smem_bytes = tma_smem_bytes(c->lat, t);
+    if (t.smem_bytes < 0) return false;
+    const int nb = tma_max_blocks_per_sm(c->lat, c->eq, c->bulk, t);
+    if (nb < 1) return false;
+    t.blocks = sm_count() * nb;
+    return true;
+}
+
+void drop_graph(lbm_ctx *c) {
+    if (c->graph2) {
+        cudaGraphExecDestroy(c->graph2);
+        c->graph2 = nullptr;
+    }
+}
+
+int build_graph(lbm_ctx *c) {
+    drop_graph(c);
+    cudaStream_t cap;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "graph stream");
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e1 = launch_one(c, 0, 0, cap);
+        cudaError_t e2 = launch_one(c, 1, 0, cap);
+        e = cudaStreamEndCapture(cap, &g);
+        if (e == cudaSuccess && (e1 != cudaSuccess || e2 != cudaSuccess)) e = e1 != cudaSuccess ? e1 : e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph2, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return cuda_fail("graph capture", e);
+    return LBM_OK;
+}
+
+int valid_dtype(int dtype) { return dtype == LBM_DT_F64 || dtype == LBM_DT_F32; }
+
+// Copy a caller buffer into a temporary device buffer when it lives on the host.
+struct DevBuf {
+    void *p = nullptr;
+    bool owned = false;
+    ~DevBuf() {
+        if (owned && p) cudaFree(p);
+    }
+};
+
+// Device staging buffer `slot` of a context, grown to at least `bytes`.
+int ctx_stage(lbm_ctx *c, int slot, size_t bytes, void **out) {
+    if (c->stage_cap[slot] < bytes) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->stage[slot]);
+        c->stage[slot] = nullptr;
+        c->stage_cap[slot] = 0;
+        if (cudaMalloc(&c->stage[slot], bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LBM_ENOMEM, "device staging buffer of %zu bytes", bytes);
+        }
+        c->stage_cap[slot] = bytes;
+    }
+    *out = c->stage[slot];
+    return LBM_OK;
+}
+
+int stage_in(const void *src, size_t bytes, int on_device, cudaStream_t s, DevBuf &out) {
+    if (on_device) {
+        out.p = const_cast<void *>(src);
+        return LBM_OK;
+    }
+    if (cudaMalloc(&out.p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ENOMEM, "device staging buffer of %zu bytes", bytes);
+    }
+    out.owned = true;
+    CK(cudaMemcpyAsync(out.p, src, bytes, cudaMemcpyHostToDevice, s), "host to device copy");
+    return LBM_OK;
+}
+
+std::string tune_key(lbm_ctx *c) {
+    cudaDeviceProp prop;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&prop, dev);
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s|D%d|P%d|E%d|B%d|%lldx%lldx%lld", prop.name, c->D, c->prec, c->eq, c->bulk,
+             (long long)c->dims[0], (long long)c->dims[1], (long long)c->dims[2]);
+    std::string k = buf;
+    for (char &ch : k)
+        if (ch == ' ') ch = '_';
+    return k;
+}
+
+std::mutex g_tune_mu;
+std::map<std::string, std::vector<int>> g_tune_cache;
+
+const char *tune_file() {
+    const char *e = getenv("LBM_TUNE_CACHE");
+    return (e && *e) ? e : nullptr;
+}
+
+void tune_cache_load() {
+    const char *path = tune_file();
+    if (!path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char key[512];
+    int v[8];
+    while (fscanf(f, "%511s %d %d %d %d %d %d %d %d", key, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7]) == 9)
+        g_tune_cache[key] = std::vector<int>(v, v + 8);
+    fclose(f);
+}
+
+void tune_cache_store(const std::string &key, const std::vector<int> &v) {
+    g_tune_cache[key] = v;
+    const char *path = tune_file();
+    if (!path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s", key.c_str());
+    for (int x : v) fprintf(f, " %d", x);
+    fprintf(f, "\n");
+    fclose(f);
+}
+
+// Apply a cached or tuned shape: {kernel, threads, blocks, stages, rows, seg, cap, smem}.
+void apply_shape(lbm_ctx *c, const std::vector<int> &v) {
+    c->kernel = v[0];
+    if (v[0] == 2) {
+        c->tma.threads = v[1];
+        c->tma.blocks = v[2];
+        c->tma.stages = v[3];
+        c->tma.rows = v[4];
+        c->tma.seg = v[5];
+        c->tma.cap = v[6];
+        c->tma.smem_bytes = v[7];
+        tma_prepare(c->lat, c->eq, c->bulk, c->tma.cap, c->tma.smem_bytes);
+    } else {
+        c->gen_threads = v[1];
+        c->gen_blocks = v[2];
+    }
+}
+
+float time_steps(lbm_ctx *c, int nsteps) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, c->stream);
+    for (int s = 0; s < nsteps; ++s) launch_one(c, (int)((c->step + s) & 1), 0, c->stream);
+    cudaEventRecord(e1, c->stream);
+    float ms = -1;
+    if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    if (cudaGetLastError() != cudaSuccess) ms = -1;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+}
+
+int autotune(lbm_ctx *c) {
+    const size_t bytes = (size_t)c->Q * c->lat.plane * esize_of(c->prec);
+    void *backup = nullptr;
+    if (cudaMalloc(&backup, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ENOMEM, "autotune backup of %zu bytes", bytes);
+    }
+    CK(cudaMemcpyAsync(backup, c->lat.A, bytes, cudaMemcpyDeviceToDevice, c->stream), "autotune backup");
+    std::vector<std::vector<int>> cands;
+    const int es = esize_of(c->prec);
+    const int U = 16 / es;
+    const int64_t rowb = c->lat.nx * (int64_t)es;
+    for (int th : {128, 256}) {
+        int g = (int)std::min<int64_t>((c->ncell + th - 1) / th, (int64_t)sm_count() * 16);
+        cands.push_back({1, th, std::max(g, 1), 0, 0, 0, 0, 0});
+    }
+    if (tma_supported(c->lat)) {
+        for (int cap : {1024, 2048, 4096, 8192}) {
+            std::vector<std::pair<int, int>> geo;  // (rows, seg)
+            if (rowb <= cap) {
+                const int rmax = (int)std::min<int64_t>(cap / rowb, c->lat.ny);
+                geo.push_back({rmax, (int)c->lat.nx});
+                if (rmax > 1) geo.push_back({std::max(1, rmax / 2), (int)c->lat.nx});
+            } else {
+                geo.push_back({1, (cap / es - 2 * U) / U * U});
+            }
+            for (auto rs : geo)
+                for (int th : {128, 192, 256})
+                    for (int st : {2, 3, 4, 6, 8}) {
+                        TmaShape t{};
+                        t.threads = th;
+                        t.stages = st;
+                        t.rows = rs.first;
+                        t.seg = rs.second;
+                        t.cap = cap;
+                        t.smem_bytes = tma_smem_bytes(c->lat, t);
+                        if (t.smem_bytes < 0) continue;
+                        const int nb = tma_max_blocks_per_sm(c->lat, c->eq, c->bulk, t);
+                        if (nb < 1) continue;
+                        // keep 2..4 stages per block only when several blocks share an SM
+                        if (nb * st > 16) continue;
+                        t.blocks = sm_count() * nb;
+                        cands.push_back({2, t.threads, t.blocks, t.stages, t.rows, t.seg, t.cap, t.smem_bytes});
+                    }
+        }
+    }
+    const int saved_kernel = c->kernel;
+    const TmaShape saved_tma = c->tma;
+    const int saved_gt = c->gen_threads, saved_gb = c->gen_blocks;
+    float best = 1e30f;
+    std::vector<int> bestv;
+    const int reps = c->ncell > (1 << 22) ? 4 : 10;
+    for (const auto &v : cands) {
+        apply_shape(c, v);
+        if (time_steps(c, 2) < 0) continue;
+        const float ms = time_steps(c, reps);
+        if (ms > 0 && ms < best) {
+            best = ms;
+            bestv = v;
+        }
+    }
+    cudaGetLastError();
+    CK(cudaMemcpyAsync(c->lat.A, backup, bytes, cudaMemcpyDeviceToDevice, c->stream), "autotune restore");
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int32_t), c->stream), "status reset");
+    CK(cudaStreamSynchronize(c->stream), "autotune sync");
+    cudaFree(backup);
+    if (bestv.empty()) {
+        c->kernel = saved_kernel;
+        c->tma = saved_tma;
+        c->gen_threads = saved_gt;
+        c->gen_blocks = saved_gb;
+        return fail(LBM_ECUDA, "autotune found no runnable launch shape");
+    }
+    apply_shape(c, bestv);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_cache_store(tune_key(c), bestv);
+    }
+    drop_graph(c);
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbm_last_error(void) { return g_err.c_str(); }
+
+int lbm_version(void) { return 10000; }
+
+int lbm_create(lbm_ctx **out, int lattice, const int64_t dims[3], double tau, int eq_kind,
+               int bulk_corr, int precision, double rho0, void *cuda_stream) {
+    if (!out || !dims) return fail(LBM_EINVAL, "null argument");
+    *out = nullptr;
+    if (lattice != LBM_D2Q9 && lattice != LBM_D3Q27) return fail(LBM_EINVAL, "bad lattice %d", lattice);
+    if (eq_kind < 0 || eq_kind > 2) return fail(LBM_EINVAL, "bad eq_kind %d", eq_kind);
+    if (bulk_corr != 0 && bulk_corr != 1) return fail(LBM_EINVAL, "bulk_corr must be 0 or 1");
+    if (precision < 0 || precision > 2) return fail(LBM_EINVAL, "bad precision %d", precision);
+    if (!(tau > 0.5) || !std::isfinite(tau)) return fail(LBM_EINVAL, "tau must be a finite value > 1/2 (got %g)", tau);
+    if (!(rho0 > 0) || !std::isfinite(rho0)) return fail(LBM_EINVAL, "rho0 must be positive");
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 1 || dims[a] > (1 << 30)) return fail(LBM_EINVAL, "dims[%d] = %lld out of range", a, (long long)dims[a]);
+    if (lattice == LBM_D2Q9 && dims[2] != 1) return fail(LBM_EINVAL, "D2Q9 needs dims[2] == 1");
+    const int64_t ncell = dims[0] * dims[1] * dims[2];
+    if (ncell / dims[0] / dims[1] != dims[2] || ncell > ((int64_t)1 << 40)) return fail(LBM_EINVAL, "lattice too large");
+    lbm_ctx *c = new lbm_ctx();
+    c->lattice = lattice;
+    c->D = lattice == LBM_D2Q9 ? 2 : 3;
+    c->Q = c->D == 2 ? 9 : 27;
+    c->eq = eq_kind;
+    c->bulk = bulk_corr;
+    c->prec = precision;
+    for (int a = 0; a < 3; ++a) c->dims[a] = dims[a];
+    c->ncell = ncell;
+    c->tau = tau;
+    c->rho0 = rho0;
+    c->omega0 = 1.0 / tau;
+    c->six_nu = 6.0 * (tau - 0.5) / 3.0;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    const int es = esize_of(precision);
+    const int64_t align = 256 / es;
+    const int64_t plane = (ncell + align - 1) / align * align;
+    c->lat.plane = plane;
+    c->lat.nx = (int)dims[0];
+    c->lat.ny = (int)dims[1];
+    c->lat.nz = (int)dims[2];
+    c->lat.ncell = ncell;
+    c->lat.D = c->D;
+    c->lat.P = precision;
+    const size_t bytes = (size_t)c->Q * plane * es;
+    if (cudaMalloc(&c->lat.A, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return fail(LBM_ENOMEM, "population storage of %zu bytes", bytes);
+    }
+    bool ok = cudaMalloc(&c->partials, sizeof(double) * kDiagWords * kPartialsCap) == cudaSuccess &&
+              cudaMalloc(&c->hist, sizeof(double) * 8 * kHistCap) == cudaSuccess &&
+              cudaMalloc(&c->scratch, sizeof(double) * 8) == cudaSuccess &&
+              cudaMalloc(&c->status, sizeof(int32_t)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        lbm_destroy(c);
+        return fail(LBM_ENOMEM, "diagnostics buffers");
+    }
+    if (cudaMemsetAsync(c->lat.A, 0, bytes, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->status, 0, sizeof(int32_t), c->stream) != cudaSuccess) {
+        lbm_destroy(c);
+        return cuda_fail("initial memset", cudaGetLastError());
+    }
+    c->gen_threads = 256;
+    c->gen_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((ncell + 255) / 256, (int64_t)sm_count() * 16));
+    c->kernel = 1;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        static bool loaded = false;
+        if (!loaded) {
+            tune_cache_load();
+            loaded = true;
+        }
+        auto it = g_tune_cache.find(tune_key(c));
+        if (it != g_tune_cache.end()) {
+            apply_shape(c, it->second);
+            if (c->kernel == 2 && !tma_supported(c->lat)) c->kernel = 1;
+            *out = c;
+            return LBM_OK;
+        }
+    }
+    if (tma_supported(c->lat) && default_tma_shape(c, c->tma)) {
+        tma_prepare(c->lat, c->eq, c->bulk, c->tma.cap, c->tma.smem_bytes);
+        c->kernel = 2;
+    }
+    cudaGetLastError();
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_set_option(lbm_ctx *c, int option, int64_t value) {
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    switch (option) {
+    case LBM_OPT_DIAG_EVERY:
+        if (value < 0) return fail(LBM_EINVAL, "diag_every must be >= 0");
+        c->diag_every = value;
+        return LBM_OK;
+    case LBM_OPT_KERNEL:
+        if (value < 0 || value > 2) return fail(LBM_EINVAL, "kernel must be 0, 1 or 2");
+        if (value == 2 && !tma_supported(c->lat))
+            return fail(LBM_EINVAL, "TMA row kernel needs Nx * sizeof(storage) to be a multiple of 16");
+        c->kernel_opt = (int)value;
+        if (value == 1) c->kernel = 1;
+        if (value == 2 || value == 0) {
+            if (tma_supported(c->lat)) {
+                if (c->tma.smem_bytes <= 0 && !default_tma_shape(c, c->tma))
+                    return fail(LBM_ECUDA, "no TMA launch shape fits this lattice");
+                tma_prepare(c->lat, c->eq, c->bulk, c->tma.cap, c->tma.smem_bytes);
+                c->kernel = 2;
+            } else {
+                c->kernel = 1;
+            }
+        }
+        drop_graph(c);
+        return LBM_OK;
+    case LBM_OPT_USE_GRAPH:
+        c->use_graph = value != 0;
+        drop_graph(c);
+        return LBM_OK;
+    case LBM_OPT_TUNE:
+        if (value) return ctx_sticky(c, autotune(c));
+        return LBM_OK;
+    default:
+        return fail(LBM_EINVAL, "unknown option %d", option);
+    }
+}
+
+int lbm_init_fields(lbm_ctx *c, const void *rho, const void *u, int dtype, int on_device) {
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (!rho || !u || !valid_dtype(dtype)) return fail(LBM_EINVAL, "bad field arguments");
+    const size_t es = dtype == LBM_DT_F64 ? 8 : 4;
+    const void *dr = rho, *du = u;
+    if (!on_device) {
+        void *pr, *pu;
+        if ((rc = ctx_stage(c, 0, es * c->ncell, &pr))) return ctx_sticky(c, rc);
+        if ((rc = ctx_stage(c, 1, es * c->ncell * c->D, &pu))) return ctx_sticky(c, rc);
+        CK(cudaMemcpyAsync(pr, rho, es * c->ncell, cudaMemcpyHostToDevice, c->stream), "field upload");
+        CK(cudaMemcpyAsync(pu, u, es * c->ncell * c->D, cudaMemcpyHostToDevice, c->stream), "field upload");
+        dr = pr;
+        du = pu;
+    }
+    cudaError_t e = init_fields(c->lat, c->eq, c->rho0, dr, du, dtype, c->stream);
+    if (e != cudaSuccess) return ctx_sticky(c, cuda_fail("init kernel", e));
+    c->step = 0;
+    c->hist_count = 0;
+    drop_graph(c);
+    if (!on_device) {
+        // host buffers (pinned ones included) are only borrowed for the call
+        e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return ctx_sticky(c, cuda_fail("init sync", e));
+    }
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx *c, int64_t n) {
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (n < 0) return fail(LBM_EINVAL, "n must be >= 0");
+    int64_t ndiag = 0;
+    int64_t s = 0;
+    if (c->use_graph && c->diag_every == 0) {
+        if ((c->step & 1) && n > 0) {
+            cudaError_t e = launch_one(c, 1, 0, c->stream);
+            if (e != cudaSuccess) return ctx_sticky(c, cuda_fail("step launch", e));
+            ++c->step;
+            ++s;
+        }
+        if (n - s >= 2 && !c->graph2) {
+            if ((rc = build_graph(c))) return ctx_sticky(c, rc);
+        }
+        while (n - s >= 2) {
+            cudaError_t e = cudaGraphLaunch(c->graph2, c->stream);
+            if (e != cudaSuccess) return ctx_sticky(c, cuda_fail("graph launch", e));
+            c->step += 2;
+            s += 2;
+        }
+    }
+    for (; s < n; ++s) {
+        const int odd = (int)(c->step & 1);
+        const int diag = c->diag_every > 0 && (c->step % c->diag_every) == 0;
+        cudaError_t e = launch_one(c, odd, diag, c->stream);
+        if (e != cudaSuccess) return ctx_sticky(c, cuda_fail("step launch", e));
+        if (diag) {
+            e = diag_finalize(c->partials, launch_blocks(c), c->step, c->hist + 8 * (c->hist_count % kHistCap), c->stream);
+            if (e != cudaSuccess) return ctx_sticky(c, cuda_fail("diagnostics launch", e));
+            ++c->hist_count;
+            ++ndiag;
+        }
+        ++c->step;
+    }
+    if (ndiag > 0) {
+        if ((rc = read_status(c))) return rc;
+        const int64_t take = std::min<int64_t>(ndiag, kHistCap);
+        std::vector<double> rec(8 * take);
+        for (int64_t q = 0; q < take; ++q) {
+            const int64_t slot = (c->hist_count - take + q) % kHistCap;
+            cudaError_t e = cudaMemcpy(&rec[8 * q], c->hist + 8 * slot, 8 * sizeof(double), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return ctx_sticky(c, cuda_fail("diagnostics copy", e));
+        }
+        for (int64_t q = 0; q < take; ++q)
+            if (rec[8 * q + 6] > 0 || !std::isfinite(rec[8 * q + 0]))
+                return fail(LBM_ENONFINITE, "non-finite state at step %lld", (long long)rec[8 * q + 7]);
+    }
+    return LBM_OK;
+}
+
+int lbm_moments(lbm_ctx *c, void *rho, void *u, int dtype, int on_device) {
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (!rho || !u || !valid_dtype(dtype)) return fail(LBM_EINVAL, "bad field arguments");
+    const size_t es = dtype == LBM_DT_F64 ? 8 : 4;
+    void *dr = rho, *du = u;
+    if (!on_device) {
+        if ((rc = ctx_stage(c, 0, es * c->ncell, &dr))) return ctx_sticky(c, rc);
+        if ((rc = ctx_stage(c, 1, es * c->ncell * c->D, &du))) return ctx_sticky(c, rc);
+    }
+    cudaError_t e = moments(c->lat, c->rho0, (int)(c->step & 1), dr, du, dtype, c->stream);
+    if (e != cudaSuccess) return ctx_sticky(c, cuda_fail("moments kernel", e));
+    if (!on_device) {
+        CK(cudaMemcpyAsync(rho, dr, es * c->ncell, cudaMemcpyDeviceToHost, c->stream), "moments copy");
+        CK(cudaMemcpyAsync(u, du, es * c->ncell * c->D, cudaMemcpyDeviceToHost, c->stream), "moments copy");
+        CK(cudaStreamSynchronize(c->stream), "moments sync");
+    }
+    return LBM_OK;
+}
+
+static void fill_diag(const double *r, lbm_diag *out) {
+    out->mass = r[0];
+    out->momentum[0] = r[1];
+    out->momentum[1] = r[2];
+    out->momentum[2] = r[3];
+    out->kinetic = r[4];
+    out->max_u = r[5];
+    out->nonfinite = (int64_t)r[6];
+    out->step = (int64_t)r[7];
+}
+
+int lbm_diagnostics(lbm_ctx *c, lbm_diag *out) {
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (!out) return fail(LBM_EINVAL, "null output");
+    const int blocks = diag_blocks_generic(c->ncell);
+    cudaError_t e = diag_state(c->lat, c->rho0, (int)(c->step & 1), c->partials, blocks, c->stream);
+    if (e == cudaSuccess) e = diag_finalize(c->partials, blocks, c->step, c->scratch, c->stream);
+    if (e != cudaSuccess) return ctx_sticky(c, cuda_fail("diagnostics kernel", e));
+    double r[8];
+    CK(cudaMemcpyAsync(r, c->scratch, sizeof r, cudaMemcpyDeviceToHost, c->stream), "diagnostics copy");
+    CK(cudaStreamSynchronize(c->stream), "diagnostics sync");
+    if ((rc = read_status(c))) return rc;
+    fill_diag(r, out);
+    return LBM_OK;
+}
+
+int lbm_diag_history(lbm_ctx *c, lbm_diag *out, int64_t max, int64_t *count) {
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (!count || (max > 0 && !out) || max < 0) return fail(LBM_EINVAL, "bad history arguments");
+    const int64_t avail = std::min<int64_t>(c->hist_count, kHistCap);
+    *count = avail;
+    const int64_t take = std::min<int64_t>(avail, max);
+    if (take == 0) return LBM_OK;
+    std::vector<double> all(8 * kHistCap);
+    CK(cudaStreamSynchronize(c->stream), "history sync");
+    CK(cudaMemcpy(all.data(), c->hist, sizeof(double) * 8 * kHistCap, cudaMemcpyDeviceToHost), "history copy");
+    const int64_t first = c->hist_count - avail;
+    for (int64_t q = 0; q < take; ++q) fill_diag(&all[8 * ((first + q) % kHistCap)], &out[q]);
+    return LBM_OK;
+}
+
+static size_t pop_esize(lbm_ctx *c, int dtype) {
+    return dtype == LBM_DT_F64 ? 8 : (dtype == LBM_DT_F32 ? 4 : (size_t)esize_of(c->prec));
+}
+
+int lbm_get_populations(lbm_ctx *c, void *f, int dtype, int on_device) {
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (!f || !(valid_dtype(dtype) || dtype == LBM_DT_STORAGE)) return fail(LBM_EINVAL, "bad population arguments");
+    const size_t bytes = pop_esize(c, dtype) * c->Q * c->ncell;
+    void *d = f;
+    DevBuf b;
+    if (!on_device) {
+        if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LBM_ENOMEM, "population staging of %zu bytes", bytes);
+        }
+        b.owned = true;
+        d = b.p;
+    }
+    cudaError_t e = get_populations(c->lat, c->rho0, (int)(c->step & 1), d, dtype, c->stream);
+    if (e != cudaSuccess) return ctx_sticky(c, cuda_fail("population export", e));
+    if (!on_device) {
+        CK(cudaMemcpyAsync(f, d, bytes, cudaMemcpyDeviceToHost, c->stream), "population copy");
+        CK(cudaStreamSynchronize(c->stream), "population sync");
+    }
+    return LBM_OK;
+}
+
+int lbm_set_populations(lbm_ctx *c, const void *f, int dtype, int on_device) {
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (!f || !(valid_dtype(dtype) || dtype == LBM_DT_STORAGE)) return fail(LBM_EINVAL, "bad population arguments");
+    const size_t bytes = pop_esize(c, dtype) * c->Q * c->ncell;
+    DevBuf b;
+    if ((rc = stage_in(f, bytes, on_device, c->stream, b))) return ctx_sticky(c, rc);
+    cudaError_t e = set_populations(c->lat, c->rho0, (int)(c->step & 1), b.p, dtype, c->stream);
+    if (e != cudaSuccess) return ctx_sticky(c, cuda_fail("population import", e));
+    c->hist_count = 0;
+    if (!on_device) CK(cudaStreamSynchronize(c->stream), "population sync");
+    return LBM_OK;
+}
+
+int lbm_set_step_count(lbm_ctx *c, int64_t step) {
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (step < 0) return fail(LBM_EINVAL, "step must be >= 0");
+    if ((step & 1) != (c->step & 1)) {
+        // the AA layout depends on the step parity: move the canonical state across
+        void *tmp = nullptr;
+        const size_t bytes = sizeof(double) * c->Q * c->ncell;
+        if ((rc = ctx_stage(c, 0, bytes, &tmp))) return ctx_sticky(c, rc);
+        cudaError_t e = get_populations(c->lat, c->rho0, (int)(c->step & 1), tmp, LBM_DT_F64, c->stream);
+        if (e == cudaSuccess) e = set_populations(c->lat, c->rho0, (int)(step & 1), tmp, LBM_DT_F64, c->stream);
+        if (e != cudaSuccess) return ctx_sticky(c, cuda_fail("re-layout", e));
+    }
+    c->step = step;
+    drop_graph(c);
+    return LBM_OK;
+}
+
+int lbm_sample_populations(lbm_ctx *c, const int64_t *cells, int64_t count, double *out) {
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (count < 0 || (count > 0 && (!cells || !out))) return fail(LBM_EINVAL, "bad sample arguments");
+    if (count == 0) return LBM_OK;
+    for (int64_t k = 0; k < count; ++k)
+        if (cells[k] < 0 || cells[k] >= c->ncell) return fail(LBM_EINVAL, "cell index %lld out of range", (long long)cells[k]);
+    DevBuf dc, dout;
+    if ((rc = stage_in(cells, sizeof(int64_t) * count, 0, c->stream, dc))) return ctx_sticky(c, rc);
+    if (cudaMalloc(&dout.p, sizeof(double) * c->Q * count) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ENOMEM, "sample staging");
+    }
+    dout.owned = true;
+    cudaError_t e = sample_populations(c->lat, c->rho0, (int)(c->step & 1), (const int64_t *)dc.p, count,
+                                       (double *)dout.p, c->stream);
+    if (e != cudaSuccess) return ctx_sticky(c, cuda_fail("sample kernel", e));
+    CK(cudaMemcpyAsync(out, dout.p, sizeof(double) * c->Q * count, cudaMemcpyDeviceToHost, c->stream), "sample copy");
+    CK(cudaStreamSynchronize(c->stream), "sample sync");
+    return LBM_OK;
+}
+
+int lbm_step_count(lbm_ctx *c, int64_t *out) {
+    if (!c || !out) return fail(LBM_EINVAL, "null argument");
+    *out = c->step;
+    return LBM_OK;
+}
+
+int lbm_launch_info(lbm_ctx *c, int64_t out[8]) {
+    if (!c || !out) return fail(LBM_EINVAL, "null argument");
+    out[0] = c->kernel;
+    if (c->kernel == 2) {
+        out[1] = c->tma.threads;
+        out[2] = c->tma.blocks;
+        out[3] = c->tma.stages;
+        out[4] = c->tma.rows;
+        out[5] = c->tma.seg;
+        out[6] = c->tma.smem_bytes;
+    } else {
+        out[1] = c->gen_threads;
+        out[2] = c->gen_blocks;
+        out[3] = out[4] = out[5] = out[6] = 0;
+    }
+    out[7] = (int64_t)c->Q * c->lat.plane * esize_of(c->prec);
+    return LBM_OK;
+}
+
+int lbm_set_launch_shape(lbm_ctx *c, const int64_t shape[6]) {
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    if (!shape) return fail(LBM_EINVAL, "null shape");
+    if (shape[1] < 32 || shape[1] > 256 || shape[1] % 32) return fail(LBM_EINVAL, "threads must be a multiple of 32 in [32, 256]");
+    if (shape[0] == 1) {
+        c->kernel = 1;
+        c->gen_threads = (int)shape[1];
+        c->gen_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((c->ncell + shape[1] - 1) / shape[1],
+                                                                    (int64_t)sm_count() * 16));
+        drop_graph(c);
+        return LBM_OK;
+    }
+    if (shape[0] != 2) return fail(LBM_EINVAL, "kernel must be 1 or 2");
+    if (!tma_supported(c->lat)) return fail(LBM_EINVAL, "TMA row kernel needs Nx * sizeof(storage) %% 16 == 0");
+    TmaShape t{};
+    t.threads = (int)shape[1];
+    t.stages = (int)shape[2];
+    t.rows = (int)std::max<int64_t>(1, shape[3]);
+    t.seg = (int)std::min<int64_t>(shape[4], c->lat.nx);
+    t.cap = (int)shape[5];
+    t.smem_bytes = tma_smem_bytes(c->lat, t);
+    if (t.smem_bytes < 0) return fail(LBM_EINVAL, "launch shape does not fit (segment, rows, cap or stages)");
+    const int nb = tma_max_blocks_per_sm(c->lat, c->eq, c->bulk, t);
+    if (nb < 1) return fail(LBM_EINVAL, "launch shape does not fit on the device");
+    t.blocks = sm_count() * nb;
+    CK(tma_prepare(c->lat, c->eq, c->bulk, t.cap, t.smem_bytes), "shared memory attribute");
+    c->tma = t;
+    c->kernel = 2;
+    drop_graph(c);
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_ctx *c) {
+    int rc = ctx_check(c);
+    if (rc) return rc;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return ctx_sticky(c, cuda_fail("sync", e));
+    return read_status(c);
+}
+
+void lbm_destroy(lbm_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    drop_graph(c);
+    cudaFree(c->lat.A);
+    cudaFree(c->partials);
+    cudaFree(c->hist);
+    cudaFree(c->scratch);
+    cudaFree(c->status);
+    cudaFree(c->stage[0]);
+    cudaFree(c->stage[1]);
+    cudaGetLastError();
+    delete c;
+}
+
+int lbm_selftest_bounded_wait(void *cuda_stream, int64_t timeout_ns, int32_t *status_out) {
+    if (!status_out || timeout_ns <= 0 || timeout_ns > 10000000000LL)
+        return fail(LBM_EINVAL, "bad self-test arguments");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int32_t *d = nullptr;
+    CK(cudaMalloc(&d, sizeof(int32_t)), "self-test buffer");
+    cudaError_t e = cudaMemsetAsync(d, 0x7f, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = selftest_wait(timeout_ns, d, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(status_out, d, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail("self-test", e);
+    return LBM_OK;
+}
+
+// ------------------------------------------------------------------------------ batch
+
+static int batch_check(lbm_batch *b) {
+    if (!b) return fail(LBM_EINVAL, "null batch");
+    if (b->sticky) return fail(LBM_ESTATE, "batch is in an error state (%d); destroy it", b->sticky);
+    return LBM_OK;
+}
+
+static int batch_sticky(lbm_batch *b, int code) {
+    if (code == LBM_ECUDA || code == LBM_ETIMEOUT || code == LBM_ENOMEM) b->sticky = code;
+    return code;
+}
+
+int lbm_batch_create(lbm_batch **out, int lattice, int64_t count, const int32_t *dims,
+                     const double *tau, int eq_kind, int bulk_corr, int precision, double rho0,
+                     void *cuda_stream) {
+    if (!out || !dims || !tau) return fail(LBM_EINVAL, "null argument");
+    *out = nullptr;
+    if (lattice != LBM_D2Q9 && lattice != LBM_D3Q27) return fail(LBM_EINVAL, "bad lattice %d", lattice);
+    if (count < 1 || count > (1 << 24)) return fail(LBM_EINVAL, "count out of range");
+    if (eq_kind < 0 || eq_kind > 2) return fail(LBM_EINVAL, "bad eq_kind %d", eq_kind);
+    if (bulk_corr != 0 && bulk_corr != 1) return fail(LBM_EINVAL, "bulk_corr must be 0 or 1");
+    if (precision != LBM_F64) return fail(LBM_EINVAL, "the batched path stores FP64 (precision must be LBM_F64)");
+    if (!(rho0 > 0) || !std::isfinite(rho0)) return fail(LBM_EINVAL, "rho0 must be positive");
+    const int D = lattice == LBM_D2Q9 ? 2 : 3;
+    std::vector<int64_t> cs(count + 1, 0);
+    for (int64_t k = 0; k < count; ++k) {
+        for (int a = 0; a < 3; ++a)
+            if (dims[3 * k + a] < 1 || dims[3 * k + a] > 65536) return fail(LBM_EINVAL, "instance %lld: bad dims", (long long)k);
+        if (D == 2 && dims[3 * k + 2] != 1) return fail(LBM_EINVAL, "instance %lld: D2Q9 needs Nz == 1", (long long)k);
+        if (!(tau[k] > 0.5) || !std::isfinite(tau[k])) return fail(LBM_EINVAL, "instance %lld: tau must be > 1/2", (long long)k);
+        cs[k + 1] = cs[k] + (int64_t)dims[3 * k] * dims[3 * k + 1] * dims[3 * k + 2];
+    }
+    lbm_batch *b = new lbm_batch();
+    b->lattice = lattice;
+    b->D = D;
+    b->Q = D == 2 ? 9 : 27;
+    b->eq = eq_kind;
+    b->bulk = bulk_corr;
+    b->count = count;
+    b->total = cs[count];
+    b->rho0 = rho0;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    b->dims.assign(dims, dims + 3 * count);
+    b->cell_start = cs;
+    std::vector<double> om(count), sn(count);
+    for (int64_t k = 0; k < count; ++k) {
+        om[k] = 1.0 / tau[k];
+        sn[k] = 6.0 * (tau[k] - 0.5) / 3.0;
+    }
+    // Greedy longest-first assignment of whole instances to blocks.
+    const int nb = (int)std::min<int64_t>(count, (int64_t)sm_count() * 2);
+    std::vector<int32_t> idx(count);
+    for (int64_t k = 0; k < count; ++k) idx[k] = (int32_t)k;
+    std::sort(idx.begin(), idx.end(), [&](int32_t a, int32_t c) {
+        const int64_t na = cs[a + 1] - cs[a], nc = cs[c + 1] - cs[c];
+        return na != nc ? na > nc : a < c;
+    });
+    using Item = std::pair<int64_t, int>;
+    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
+    for (int q = 0; q < nb; ++q) heap.push({0, q});
+    std::vector<std::vector<int32_t>> own(nb);
+    for (int32_t k : idx) {
+        Item it = heap.top();
+        heap.pop();
+        own[it.second].push_back(k);
+        it.first += cs[k + 1] - cs[k];
+        heap.push(it);
+    }
+    std::vector<int32_t> order;
+    std::vector<int32_t> bstart(nb + 1, 0);
+    int64_t maxload = 0;
+    for (int q = 0; q < nb; ++q) {
+        int64_t load = 0;
+        for (int32_t k : own[q]) {
+            order.push_back(k);
+            load += cs[k + 1] - cs[k];
+        }
+        maxload = std::max(maxload, load);
+        bstart[q + 1] = (int32_t)order.size();
+    }
+    b->blocks = nb;
+    b->max_load = maxload;
+    b->mean_load = b->total / nb;
+    const size_t arena_bytes = sizeof(double) * (size_t)b->Q * b->total;
+    bool ok = cudaMalloc(&b->arena, arena_bytes) == cudaSuccess &&
+              cudaMalloc(&b->d_cell_start, sizeof(int64_t) * (count + 1)) == cudaSuccess &&
+              cudaMalloc(&b->d_dims, sizeof(int32_t) * 3 * count) == cudaSuccess &&
+              cudaMalloc(&b->d_omega, sizeof(double) * count) == cudaSuccess &&
+              cudaMalloc(&b->d_sixnu, sizeof(double) * count) == cudaSuccess &&
+              cudaMalloc(&b->d_order, sizeof(int32_t) * count) == cudaSuccess &&
+              cudaMalloc(&b->d_block_start, sizeof(int32_t) * (nb + 1)) == cudaSuccess &&
+              cudaMalloc(&b->d_status, sizeof(int32_t) * count) == cudaSuccess &&
+              cudaMalloc(&b->d_tw_off, sizeof(int64_t) * count) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        lbm_batch_destroy(b);
+        return fail(LBM_ENOMEM, "batch storage of %zu bytes", arena_bytes);
+    }
+    cudaError_t e = cudaSuccess;
+    auto up = [&](void *d, const void *h, size_t n) {
+        if (e == cudaSuccess) e = cudaMemcpy(d, h, n, cudaMemcpyHostToDevice);
+    };
+    up(b->d_cell_start, cs.data(), sizeof(int64_t) * (count + 1));
+    up(b->d_dims, dims, sizeof(int32_t) * 3 * count);
+    up(b->d_omega, om.data(), sizeof(double) * count);
+    up(b->d_sixnu, sn.data(), sizeof(double) * count);
+    up(b->d_order, order.data(), sizeof(int32_t) * count);
+    up(b->d_block_start, bstart.data(), sizeof(int32_t) * (nb + 1));
+    if (e == cudaSuccess) e = cudaMemset(b->arena, 0, arena_bytes);
+    if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int32_t) * count);
+    if (e != cudaSuccess) {
+        lbm_batch_destroy(b);
+        return cuda_fail("batch upload", e);
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_init_fields(lbm_batch *b, const void *rho, const void *u, int dtype, int on_device) {
+    int rc = batch_check(b);
+    if (rc) return rc;
+    if (!rho || !u || !valid_dtype(dtype)) return fail(LBM_EINVAL, "bad field arguments");
+    const size_t es = dtype == LBM_DT_F64 ? 8 : 4;
+    DevBuf dr, du;
+    if ((rc = stage_in(rho, es * b->total, on_device, b->stream, dr))) return batch_sticky(b, rc);
+    if ((rc = stage_in(u, es * b->total * b->D, on_device, b->stream, du))) return batch_sticky(b, rc);
+    cudaError_t e = batch_init(b->arena, b->d_cell_start, b->d_dims, b->count, b->D, b->eq, b->rho0, dr.p, du.p,
+                               dtype, b->total, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int32_t) * b->count, b->stream);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return batch_sticky(b, cuda_fail("batch init", e));
+    b->step = 0;
+    return LBM_OK;
+}
+
+int lbm_batch_set_probe(lbm_batch *b, const int32_t *kvec, int64_t every_k) {
+    int rc = batch_check(b);
+    if (rc) return rc;
+    if (!kvec || every_k < 1) return fail(LBM_EINVAL, "bad probe arguments");
+    std::vector<double2> tw;
+    std::vector<int64_t> off(b->count);
+    const double twopi = 6.283185307179586476925286766559;
+    for (int64_t k = 0; k < b->count; ++k) {
+        off[k] = (int64_t)tw.size();
+        for (int a = 0; a < 3; ++a) {
+            const int n = b->dims[3 * k + a];
+            const int64_t m = kvec[3 * k + a];
+            for (int x = 0; x < n; ++x) {
+                const int64_t q = ((m * x) % n + n) % n;  // exact phase index
+                const double ph = twopi * (double)q / (double)n;
+                tw.push_back(make_double2(cos(ph), -sin(ph)));
+            }
+        }
+    }
+    if (b->d_tw) cudaFree(b->d_tw);
+    b->d_tw = nullptr;
+    if (cudaMalloc(&b->d_tw, sizeof(double2) * tw.size()) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ENOMEM, "probe twiddles");
+    }
+    CK(cudaMemcpy(b->d_tw, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice), "twiddle upload");
+    CK(cudaMemcpy(b->d_tw_off, off.data(), sizeof(int64_t) * b->count, cudaMemcpyHostToDevice), "twiddle offsets");
+    b->every_k = every_k;
+    return LBM_OK;
+}
+
+static int batch_reserve_series(lbm_batch *b, int64_t samples) {
+    if (samples <= b->max_samples) return LBM_OK;
+    int64_t cap = std::max<int64_t>(samples, 2 * b->max_samples);
+    double *d = nullptr;
+    const size_t bytes = sizeof(double) * 8 * (size_t)b->count * cap;
+    if (cudaMalloc(&d, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ENOMEM, "probe series of %zu bytes", bytes);
+    }
+    CK(cudaMemsetAsync(d, 0, bytes, b->stream), "series clear");
+    if (b->d_series && b->max_samples > 0) {
+        CK(cudaMemcpy2DAsync(d, sizeof(double) * 8 * cap, b->d_series, sizeof(double) * 8 * b->max_samples,
+                             sizeof(double) * 8 * b->max_samples, b->count, cudaMemcpyDeviceToDevice, b->stream),
+           "series grow");
+    }
+    CK(cudaStreamSynchronize(b->stream), "series sync");
+    cudaFree(b->d_series);
+    b->d_series = d;
+    b->max_samples = cap;
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch *b, int64_t n) {
+    int rc = batch_check(b);
+    if (rc) return rc;
+    if (n < 0) return fail(LBM_EINVAL, "n must be >= 0");
+    if (n == 0) return LBM_OK;
+    if (b->every_k > 0) {
+        const int64_t last = b->step + n - 1;
+        if ((rc = batch_reserve_series(b, last / b->every_k + 1))) return batch_sticky(b, rc);
+    }
+    BatchArgs a;
+    a.arena = b->arena;
+    a.cell_start = b->d_cell_start;
+    a.dims = b->d_dims;
+    a.omega0 = b->d_omega;
+    a.six_nu = b->d_sixnu;
+    a.order = b->d_order;
+    a.block_start = b->d_block_start;
+    a.twiddle = b->d_tw;
+    a.tw_offset = b->d_tw_off;
+    a.series = b->d_series;
+    a.max_samples = b->max_samples;
+    a.status = b->d_status;
+    a.count = b->count;
+    a.D = b->D;
+    a.eq = b->eq;
+    a.bulk = b->bulk;
+    a.rho0 = b->rho0;
+    a.step0 = b->step;
+    a.nsteps = n;
+    a.every_k = b->d_tw ? b->every_k : 0;
+    // one persistent launch, captured into a graph and replayed on the object's stream
+    cudaStream_t cap;
+    CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "batch capture stream");
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t el = step_batch(a, b->blocks, b->threads, cap);
+        e = cudaStreamEndCapture(cap, &g);
+        if (e == cudaSuccess && el != cudaSuccess) e = el;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, b->stream);
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return batch_sticky(b, cuda_fail("batch launch", e));
+    b->step += n;
+    return LBM_OK;
+}
+
+int lbm_batch_probe_series(lbm_batch *b, double *out, int64_t max_samples, int64_t *nsamples) {
+    int rc = batch_check(b);
+    if (rc) return rc;
+    if (!nsamples || max_samples < 0) return fail(LBM_EINVAL, "bad series arguments");
+    const int64_t have = b->every_k > 0 ? std::min<int64_t>((b->step + b->every_k - 1) / b->every_k, b->max_samples) : 0;
+    *nsamples = have;
+    if (!out || have == 0) return LBM_OK;
+    const int64_t take = std::min(have, max_samples);
+    CK(cudaStreamSynchronize(b->stream), "series sync");
+    CK(cudaMemcpy2D(out, sizeof(double) * 8 * max_samples, b->d_series, sizeof(double) * 8 * b->max_samples,
+                    sizeof(double) * 8 * take, b->count, cudaMemcpyDeviceToHost),
+       "series copy");
+    return LBM_OK;
+}
+
+int lbm_batch_status(lbm_batch *b, int32_t *status) {
+    int rc = batch_check(b);
+    if (rc) return rc;
+    if (!status) return fail(LBM_EINVAL, "null output");
+    CK(cudaMemcpyAsync(status, b->d_status, sizeof(int32_t) * b->count, cudaMemcpyDeviceToHost, b->stream), "status copy");
+    CK(cudaStreamSynchronize(b->stream), "status sync");
+    return LBM_OK;
+}
+
+int lbm_batch_moments(lbm_batch *b, void *rho, void *u, int dtype, int on_device) {
+    int rc = batch_check(b);
+    if (rc) return rc;
+    if (!rho || !u || !valid_dtype(dtype)) return fail(LBM_EINVAL, "bad field arguments");
+    const size_t es = dtype == LBM_DT_F64 ? 8 : 4;
+    void *dr = rho, *du = u;
+    DevBuf br, bu;
+    if (!on_device) {
+        if (cudaMalloc(&br.p, es * b->total) != cudaSuccess || cudaMalloc(&bu.p, es * b->total * b->D) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LBM_ENOMEM, "moments staging");
+        }
+        br.owned = bu.owned = true;
+        dr = br.p;
+        du = bu.p;
+    }
+    cudaError_t e = batch_moments(b->arena, b->d_cell_start, b->d_dims, b->count, b->D, b->rho0, (int)(b->step & 1),
+                                  dr, du, dtype, b->total, b->stream);
+    if (e != cudaSuccess) return batch_sticky(b, cuda_fail("batch moments", e));
+    if (!on_device) {
+        CK(cudaMemcpyAsync(rho, dr, es * b->total, cudaMemcpyDeviceToHost, b->stream), "moments copy");
+        CK(cudaMemcpyAsync(u, du, es * b->total * b->D, cudaMemcpyDeviceToHost, b->stream), "moments copy");
+        CK(cudaStreamSynchronize(b->stream), "moments sync");
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_get_populations(lbm_batch *b, void *f, int dtype, int on_device) {
+    int rc = batch_check(b);
+    if (rc) return rc;
+    if (!f || !valid_dtype(dtype)) return fail(LBM_EINVAL, "bad population arguments");
+    const size_t bytes = (size_t)(dtype == LBM_DT_F64 ? 8 : 4) * b->Q * b->total;
+    void *d = f;
+    DevBuf buf;
+    if (!on_device) {
+        if (cudaMalloc(&buf.p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(LBM_ENOMEM, "population staging");
+        }
+        buf.owned = true;
+        d = buf.p;
+    }
+    cudaError_t e = batch_populations(b->arena, b->d_cell_start, b->d_dims, b->count, b->D, b->rho0,
+                                      (int)(b->step & 1), d, dtype, b->total, b->stream);
+    if (e != cudaSuccess) return batch_sticky(b, cuda_fail("batch populations", e));
+    if (!on_device) {
+        CK(cudaMemcpyAsync(f, d, bytes, cudaMemcpyDeviceToHost, b->stream), "population copy");
+        CK(cudaStreamSynchronize(b->stream), "population sync");
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_info(lbm_batch *b, int64_t *total_cells, int64_t *step) {
+    if (!b || !total_cells || !step) return fail(LBM_EINVAL, "null argument");
+    *total_cells = b->total;
+    *step = b->step;
+    return LBM_OK;
+}
+
+int lbm_batch_launch_info(lbm_batch *b, int64_t out[4]) {
+    if (!b || !out) return fail(LBM_EINVAL, "null argument");
+    out[0] = b->threads;
+    out[1] = b->blocks;
+    out[2] = b->max_load;
+    out[3] = b->mean_load;
+    return LBM_OK;
+}
+
+int lbm_batch_sync(lbm_batch *b) {
+    int rc = batch_check(b);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(b->stream), "batch sync");
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch *b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    cudaFree(b->arena);
+    cudaFree(b->d_cell_start);
+    cudaFree(b->d_dims);
+    cudaFree(b->d_omega);
+    cudaFree(b->d_sixnu);
+    cudaFree(b->d_order);
+    cudaFree(b->d_block_start);
+    cudaFree(b->d_tw);
+    cudaFree(b->d_tw_off);
+    cudaFree(b->d_series);
+    cudaFree(b->d_status);
+    cudaGetLastError();
+    delete b;
+}
+
+}  // extern "C"

@@ -1,0 +1,338 @@
+// k_tma.cuh -- the TMA row-staged fused stream-collide kernel (AA pattern, in place).
+//
+// A job is a group of `rows` consecutive x-rows of one z-plane, or one aligned segment
+// of `seg` cells of a row when the row is too long for shared memory.  For every
+// population direction b the job needs one row piece ("buffer b"):
+//   even step: plane b of the job's own rows, read at x, written back as the opposite
+//              direction's post-collision value at x;
+//   odd step:  plane opp(b) of the rows shifted by -c_b in y and z; cell x reads it at
+//              x - c_bx (pulling f_b from its neighbour) and the same cell writes its
+//              post-collision value of direction opp(b) there.
+// Every position of buffer b is read by exactly one cell of the job and written by the
+// same cell (the AA pattern's own property), so the collision runs in place in shared
+// memory and buffer b is stored back to exactly the global location it was loaded from.
+// Different jobs touch disjoint global locations, so jobs need no ordering.
+//
+// Data movement (warp specialised): the last warp of the block is the producer, the
+// others collide.  Lane b of the producer issues the cp.async.bulk copies of buffer b
+// (global -> shared, completion counted in transaction bytes on the stage's `full`
+// mbarrier) and later the cp.async.bulk stores of the same buffer (shared -> global) in
+// its own bulk async-group, so each lane orders its own store before its own refill of
+// that buffer.  Consumer warps wait on `full`, collide the job in place, fence their
+// shared-memory writes for the async proxy and arrive on the stage's `empty` mbarrier;
+// the producer then stores the stage back and refills it `stages` jobs ahead.  Rows must
+// be 16-byte multiples (Nx * sizeof(storage) % 16 == 0).
+//
+// Segmented rows (seg < Nx) carry a halo of U = 16 / sizeof(storage) cells on each side.
+// In the odd step the cells of a segment touch positions [X0 - 1, X0 + len - 1) of the
+// buffers with c_x = +1 and [X0 + 1, X0 + len + 1) of those with c_x = -1: the aligned
+// interior goes back by bulk stores and the U ragged cells at each end by plain stores,
+// so neighbouring segments never write the same location.
+#pragma once
+
+#include "lbm_common.cuh"
+#include "ptx.cuh"
+
+namespace lbmd {
+
+using lbmh::kTmaMaxStages;
+constexpr int kTmaMaxThreads = 256;  // consumer threads; one producer warp more
+
+// bufstride (elements between direction buffers) equals the compile-time buffer
+// capacity CAPB / sizeof(storage) of the kernel instantiation.
+struct TmaGeom {
+    int stages, rows, seg, nseg, ygroups, halo, rowstride, bufstride;
+    int64_t njobs;
+};
+
+constexpr int kTmaCaps[4] = {1024, 2048, 4096, 8192};  // bytes per direction buffer
+
+struct JobPos {
+    int z, y0, nrows, X0, len;
+};
+
+__device__ __forceinline__ JobPos decode_job(const lbmh::StepArgs &a, const TmaGeom &g, int64_t job) {
+    JobPos j;
+    const unsigned jb = (unsigned)job;  // njobs < 2^31 (checked on the host)
+    const unsigned rest = jb / (unsigned)g.nseg;
+    const int s = (int)(jb - rest * (unsigned)g.nseg);
+    const unsigned zq = rest / (unsigned)g.ygroups;
+    const int yg = (int)(rest - zq * (unsigned)g.ygroups);
+    j.z = (int)zq;
+    j.y0 = yg * g.rows;
+    j.nrows = min(g.rows, a.lat.ny - j.y0);
+    j.X0 = s * g.seg;
+    j.len = min(g.seg, a.lat.nx - j.X0);
+    return j;
+}
+
+// Global row (plane, y, z) of buffer b of a job.
+template <int D, typename T>
+__device__ __forceinline__ T *buffer_row(const lbmh::StepArgs &a, int b, int z, int y) {
+    constexpr int Q = qof(D);
+    const int plane = a.odd ? Q - 1 - b : b;
+    const int zz = (D == 3 && a.odd) ? wrapi(z - czo(b), a.lat.nz) : z;
+    const int yy = a.odd ? wrapi(y - cyo(b), a.lat.ny) : y;
+    return static_cast<T *>(a.lat.A) + (int64_t)plane * a.lat.plane +
+           ((int64_t)zz * a.lat.ny + yy) * a.lat.nx;
+}
+
+// Bytes of one job's loads (all buffers), for the stage's expect-tx.
+template <int D, typename T>
+__device__ __forceinline__ uint32_t tma_job_bytes(const lbmh::StepArgs &a, const TmaGeom &g, const JobPos &j) {
+    constexpr int Q = qof(D);
+    constexpr int U = 16 / (int)sizeof(T);
+    uint32_t bytes = (uint32_t)(Q * j.nrows * j.len * (int)sizeof(T));
+    if (a.odd && g.nseg > 1) bytes += (uint32_t)((2 * Q / 3) * U * (int)sizeof(T));
+    return bytes;
+}
+
+// Loads of buffer b of a job into its stage (issued by producer lane b).
+template <int D, typename T>
+__device__ __forceinline__ void tma_issue_loads(const lbmh::StepArgs &a, const TmaGeom &g,
+                                                const JobPos &j, int b, T *st, uint64_t *bar) {
+    constexpr int U = 16 / (int)sizeof(T);
+    const int nx = a.lat.nx, ny = a.lat.ny;
+    T *sbuf = st + (int64_t)b * g.bufstride;
+    int r = 0;
+    while (r < j.nrows) {
+        const int ysrc = a.odd ? wrapi(j.y0 + r - cyo(b), ny) : j.y0 + r;
+        const int run = min(j.nrows - r, ny - ysrc);
+        const T *src = buffer_row<D, T>(a, b, j.z, j.y0 + r) + j.X0;
+        bulk_g2s(sbuf + r * g.rowstride + g.halo, src, (uint32_t)(run * j.len * (int)sizeof(T)), bar);
+        r += run;
+    }
+    if (a.odd && g.nseg > 1) {
+        const T *grow = buffer_row<D, T>(a, b, j.z, j.y0);
+        if (cxo(b) == 1) {
+            const int xs = j.X0 == 0 ? nx - U : j.X0 - U;
+            bulk_g2s(sbuf, grow + xs, U * sizeof(T), bar);
+        } else if (cxo(b) == -1) {
+            const int xs = (j.X0 + j.len == nx) ? 0 : j.X0 + j.len;
+            bulk_g2s(sbuf + g.halo + j.len, grow + xs, U * sizeof(T), bar);
+        }
+    }
+}
+
+// Stores of buffer b of a job back to global memory (issued by producer lane b).
+template <int D, typename T>
+__device__ __forceinline__ void tma_issue_stores(const lbmh::StepArgs &a, const TmaGeom &g,
+                                                 const JobPos &j, int b, T *st) {
+    constexpr int U = 16 / (int)sizeof(T);
+    const int ny = a.lat.ny;
+    T *sbuf = st + (int64_t)b * g.bufstride;
+    if (!(a.odd && g.nseg > 1)) {
+        int r = 0;
+        while (r < j.nrows) {
+            const int ysrc = a.odd ? wrapi(j.y0 + r - cyo(b), ny) : j.y0 + r;
+            const int run = min(j.nrows - r, ny - ysrc);
+            T *dst = buffer_row<D, T>(a, b, j.z, j.y0 + r) + j.X0;
+            bulk_s2g(dst, sbuf + r * g.rowstride + g.halo, (uint32_t)(run * j.len * (int)sizeof(T)));
+            r += run;
+        }
+    } else {
+        T *grow = buffer_row<D, T>(a, b, j.z, j.y0);
+        if (cxo(b) == 0) {
+            bulk_s2g(grow + j.X0, sbuf + g.halo, (uint32_t)(j.len * (int)sizeof(T)));
+        } else if (j.len > U) {
+            const int off = cxo(b) == 1 ? 0 : U;  // skip the ragged end the plain stores take
+            bulk_s2g(grow + j.X0 + off, sbuf + g.halo + off, (uint32_t)((j.len - U) * (int)sizeof(T)));
+        }
+    }
+}
+
+// Plain stores of the ragged ends of segmented odd steps (U cells per buffer with c_x != 0).
+template <int D, typename T>
+__device__ __forceinline__ void tma_plain_stores(const lbmh::StepArgs &a, const TmaGeom &g,
+                                                 const JobPos &j, const T *st, int tid, int nthr) {
+    constexpr int Q = qof(D);
+    constexpr int U = 16 / (int)sizeof(T);
+    constexpr int NB = 2 * Q / 3;
+    const int nx = a.lat.nx;
+    for (int t = tid; t < NB * U; t += nthr) {
+        const int k = t / U, e = t - (t / U) * U;
+        const int b = (k >> 1) * 3 + ((k & 1) ? 2 : 0);  // k-th direction with c_x != 0
+        T *grow = buffer_row<D, T>(a, b, j.z, j.y0);
+        const T *srow = st + (int64_t)b * g.bufstride;
+        int gx, sx;
+        if (cxo(b) == 1) {
+            if (e == 0) { gx = j.X0 == 0 ? nx - 1 : j.X0 - 1; sx = g.halo - 1; }
+            else { gx = j.X0 + j.len - U + e - 1; sx = g.halo + j.len - U + e - 1; }
+        } else {
+            if (e == 0) { gx = (j.X0 + j.len == nx) ? 0 : j.X0 + j.len; sx = g.halo + j.len; }
+            else { gx = j.X0 + e; sx = g.halo + e; }
+        }
+        grow[gx] = srow[sx];
+    }
+}
+
+template <int D, int P, int EQ, bool BULK, int CAPB>
+__device__ __forceinline__ void tma_compute(const lbmh::StepArgs &a, const TmaGeom &g,
+                                            const JobPos &j, typename Storage<P>::T *st,
+                                            DiagAcc &acc, int tid, int nthr) {
+    using St = Storage<P>;
+    using T = typename St::T;
+    using R = typename St::R;
+    constexpr int Q = qof(D);
+    constexpr int bs = CAPB / (int)sizeof(T);  // compile-time offsets between buffers
+    const R rho0 = R(a.rho0), omega0 = R(a.omega0), six_nu = R(a.six_nu);
+    const bool whole = g.nseg == 1;
+    const int ncells = j.nrows * j.len;
+    // cell c of the job: row r = c / len, xl = c % len, advanced incrementally
+    int r = tid / j.len;
+    int xl = tid - r * j.len;
+    for (int c = tid; c < ncells; c += nthr) {
+        T *row = st + r * g.rowstride + g.halo;
+        int xm = xl - 1, xp = xl + 1;
+        if (whole) {
+            xm = xl == 0 ? j.len - 1 : xm;
+            xp = xl == j.len - 1 ? 0 : xp;
+        }
+        R f[Q];
+        if (!a.odd) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) f[i] = St::load(row[i * bs + xl]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int p = cxo(i) == 1 ? xm : (cxo(i) == -1 ? xp : xl);
+                f[i] = St::load(row[i * bs + p]);
+            }
+        }
+        const CellMoments<R> m = collide<D, EQ, BULK, R>(f, rho0, omega0, six_nu);
+        if (!a.odd) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) row[(Q - 1 - i) * bs + xl] = St::store(f[i]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int p = cxo(i) == 1 ? xp : (cxo(i) == -1 ? xm : xl);
+                row[(Q - 1 - i) * bs + p] = St::store(f[i]);
+            }
+        }
+        if (a.diag) acc.add(m.rho, m.u);
+        xl += nthr;
+        while (xl >= j.len) {
+            xl -= j.len;
+            ++r;
+        }
+    }
+}
+
+template <int D, int P, int EQ, bool BULK, int CAPB>
+__global__ void __launch_bounds__(kTmaMaxThreads + 32) k_step_tma(const lbmh::StepArgs a, const TmaGeom g) {
+    using T = typename Storage<P>::T;
+    constexpr int Q = qof(D);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[kTmaMaxStages];
+    __shared__ __align__(8) uint64_t empty[kTmaMaxStages];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    const int64_t stage_elems = (int64_t)Q * (CAPB / (int)sizeof(T));
+    const int S = g.stages;
+    const int64_t G = gridDim.x;
+    const int ncons = (int)blockDim.x - 32;  // consumer threads; the last warp produces
+    const int lane = threadIdx.x & 31;
+    const bool producer = (int)threadIdx.x >= ncons;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], ncons / 32);
+        }
+        fence_barrier_init();
+    }
+    __syncthreads();
+    DiagAcc acc;
+    bool failed = false;
+    if (producer) {
+        int64_t k = 0;
+        for (;; ++k) {
+            const int64_t job = blockIdx.x + k * G;
+            if (job >= g.njobs) break;
+            const int s = (int)(k % S);
+            if (k >= S) {
+                // stage s still holds job k - S: wait for its collision, store it back
+                const int64_t q = k - S;
+                const bool ok = mbar_wait_bounded(&empty[s], (uint32_t)((q / S) & 1), a.timeout_ns);
+                if (__any_sync(0xffffffffu, !ok)) {
+                    failed = true;
+                    break;
+                }
+                const JobPos jq = decode_job(a, g, blockIdx.x + q * G);
+                if (a.odd && g.nseg > 1) tma_plain_stores<D, T>(a, g, jq, sm + s * stage_elems, lane, 32);
+                if (lane < Q) {
+                    tma_issue_stores<D, T>(a, g, jq, lane, sm + s * stage_elems);
+                    bulk_commit();
+                    bulk_wait_read<0>();  // this lane's stores have read its buffer
+                }
+                __syncwarp();  // plain stores of all lanes read the stage before the refill
+            }
+            const JobPos jp = decode_job(a, g, job);
+            if (lane == 0) mbar_arrive_expect_tx(&full[s], tma_job_bytes<D, T>(a, g, jp));
+            __syncwarp();
+            if (lane < Q) tma_issue_loads<D, T>(a, g, jp, lane, sm + s * stage_elems, &full[s]);
+        }
+        const int64_t issued = k;
+        if (!failed) {
+            // store back the last stages
+            for (int64_t q = (issued > S ? issued - S : 0); q < issued; ++q) {
+                const int s = (int)(q % S);
+                const bool ok = mbar_wait_bounded(&empty[s], (uint32_t)((q / S) & 1), a.timeout_ns);
+                if (__any_sync(0xffffffffu, !ok)) {
+                    failed = true;
+                    break;
+                }
+                const JobPos jq = decode_job(a, g, blockIdx.x + q * G);
+                if (a.odd && g.nseg > 1) tma_plain_stores<D, T>(a, g, jq, sm + s * stage_elems, lane, 32);
+                if (lane < Q) {
+                    tma_issue_stores<D, T>(a, g, jq, lane, sm + s * stage_elems);
+                    bulk_commit();
+                }
+            }
+        }
+        bulk_wait_all();
+        if (failed) {
+            // let loads still in flight land before the block's shared memory is released
+            for (int64_t q = (issued > S ? issued - S : 0); q < issued; ++q)
+                (void)mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1), a.timeout_ns);
+        }
+    } else {
+        for (int64_t k = 0;; ++k) {
+            const int64_t job = blockIdx.x + k * G;
+            if (job >= g.njobs) break;
+            const int s = (int)(k % S);
+            const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((k / S) & 1), a.timeout_ns);
+            if (__any_sync(0xffffffffu, !ok)) {
+                failed = true;
+                break;
+            }
+            T *st = sm + s * stage_elems;
+            const JobPos jp = decode_job(a, g, job);
+            tma_compute<D, P, EQ, BULK, CAPB>(a, g, jp, st, acc, threadIdx.x, ncons);
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cta(&empty[s]);
+        }
+    }
+    if (failed && lane == 0) atomicExch(a.status, -5); /* LBM_ETIMEOUT */
+    if (a.diag) diag_block_store(acc, a.partials + (int64_t)blockIdx.x * lbmh::kDiagWords);
+}
+
+template <int D, int P, int CAPB>
+const void *tma_kernel_dpc(int eq, int bulk) {
+    if (eq == EQ_ENT) return bulk ? (const void *)k_step_tma<D, P, EQ_ENT, true, CAPB> : (const void *)k_step_tma<D, P, EQ_ENT, false, CAPB>;
+    if (eq == EQ_POLY2) return bulk ? (const void *)k_step_tma<D, P, EQ_POLY2, true, CAPB> : (const void *)k_step_tma<D, P, EQ_POLY2, false, CAPB>;
+    if (eq == EQ_PROD) return bulk ? (const void *)k_step_tma<D, P, EQ_PROD, true, CAPB> : (const void *)k_step_tma<D, P, EQ_PROD, false, CAPB>;
+    return nullptr;
+}
+
+template <int D, int CAPB>
+const void *tma_kernel_dc(int P, int eq, int bulk) {
+    switch (P) {
+    case P_F64: return tma_kernel_dpc<D, P_F64, CAPB>(eq, bulk);
+    case P_F32: return tma_kernel_dpc<D, P_F32, CAPB>(eq, bulk);
+    case P_F16S: return tma_kernel_dpc<D, P_F16S, CAPB>(eq, bulk);
+    default: return nullptr;
+    }
+}
+
+}  // namespace lbmd

@@ -1,0 +1,148 @@
+"""GPU parity at the full benchmark sizes, in the launch shape the benchmark uses (the
+autotuned one), on outputs the oracle can compute one by one:
+
+- D3Q27 512^3 Taylor-Green (Re = 1600), binary16 and FP32 shifted storage: populations of
+  sampled cells after 1 and 2 steps (the oracle evaluates a (2n+1)^3 patch around each
+  cell), and global mass / momentum over 40 steps.
+- D2Q9 4096^2 double shear layer, FP32: sampled cells after 1 and 2 steps.
+- 4096 batched D2Q9 instances (FP64): probe series and final populations of sampled
+  instances equal the oracle's to 1e-12.
+
+Tolerances for stored binary16 / FP32 values: each storage rounding moves f - w rho0 by
+at most half an ulp (u = 2^-11 resp. 2^-24 relative); a sampled value after n steps has
+been rounded n + 1 times directly and reaches other directions through rho and u, so
+|f_gpu - f_ref| <= (n + 2) u (|f_i - w_i| + w_i sum_j |f_j - w_j|) + n 2e-7 w_i, the last
+term for the FP32 collision arithmetic.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import core
+from paper_2303_08163_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+UNIT = {1: 2.0 ** -24, 2: 2.0 ** -11}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_library():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2303_08163_gb300 import build, lbm
+    build.build()
+    lbm.load()
+    yield
+
+
+def sample_cells(dims, count, seed):
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = dims
+    pts = [(0, 0, 0), (nx - 1, ny - 1, nz - 1), (0, ny - 1, 0), (nx - 1, 0, nz - 1)]
+    pts += [tuple(int(rng.integers(0, d)) for d in dims) for _ in range(count)]
+    return np.array(pts, dtype=np.int64)
+
+
+def flat(cells, dims):
+    nx, ny, _ = dims
+    return cells[:, 0] + nx * (cells[:, 1] + ny * cells[:, 2])
+
+
+def check_sampled(lat, D, dims, eq, bulk, tau, prec, rho_fn, u_fn, nsteps, cells):
+    got = lat.sample_populations(flat(cells, dims))
+    ref = core.local_populations(D, dims, eq, bulk, tau, nsteps, rho_fn, u_fn, cells)
+    _, w = core.lattice(D)
+    shifted = np.abs(ref - w)
+    # storage roundings of this population plus those reaching it through rho and u
+    # (bounded by the cell's total shifted magnitude), plus FP32 arithmetic per step
+    tol = ((nsteps + 2) * UNIT[prec] * (shifted + w * shifted.sum(axis=1, keepdims=True))
+           + nsteps * 2e-7 * w)
+    bad = np.abs(got - ref) > tol
+    assert not bad.any(), f"{bad.sum()} sampled populations off; worst {np.max(np.abs(got - ref) - tol):.3e}"
+
+
+@pytest.mark.parametrize("prec", [2, 1])
+def test_tgv_512_sampled_and_conservation(prec):
+    import torch
+    from paper_2303_08163_gb300 import lbm
+    n, u0 = 512, 0.1
+    nu = u0 * (n / (2 * math.pi)) / 1600.0
+    tau = 0.5 + 3 * nu
+    dims = (n, n, n)
+    rho, u = inputs.taylor_green_3d(n, u0=u0)
+    rho_fn, u_fn = inputs.taylor_green_3d_fields(n, u0=u0)
+    lat = lbm.Lattice(lbm.D3Q27, dims, tau, lbm.ENTROPIC, 0, prec)
+    lat.init_fields(rho, u)
+    lat.set_option(lbm.OPT_TUNE, 1)  # the benchmark's launch shape
+    assert lat.launch_info()["kernel"] == lbm.KERNEL_TMA
+    lat.init_fields(rho, u)
+    cells = sample_cells(dims, 48, seed=prec)
+    lat.step(1)
+    check_sampled(lat, 3, dims, core.EQ_ENTROPIC, 0, tau, prec, rho_fn, u_fn, 1, cells)
+    lat.step(1)
+    check_sampled(lat, 3, dims, core.EQ_ENTROPIC, 0, tau, prec, rho_fn, u_fn, 2, cells)
+    d0 = lat.diagnostics()
+    lat.step(40)
+    d1 = lat.diagnostics()
+    assert d1["nonfinite"] == 0
+    rel = 1e-6 if prec == 2 else 1e-9
+    assert abs(d1["mass"] - d0["mass"]) <= rel * d0["mass"]
+    assert np.all(np.abs(d1["momentum"] - d0["momentum"]) <= rel * d0["mass"])
+    lat.close()
+    del rho, u
+    torch.cuda.empty_cache()
+
+
+def test_shear_layer_4096_sampled():
+    from paper_2303_08163_gb300 import lbm
+    n = 4096
+    dims = (n, n, 1)
+    tau = 0.5 + 3e-5
+    rho, u = inputs.double_shear_layer(n)
+    rho_fn, u_fn = inputs.double_shear_layer_fields(n)
+    for eq in (core.EQ_ENTROPIC, core.EQ_POLY2):
+        lat = lbm.Lattice(lbm.D2Q9, dims, tau, eq, 0, lbm.F32)
+        lat.init_fields(rho, u)
+        lat.set_option(lbm.OPT_TUNE, 1)
+        lat.init_fields(rho, u)
+        cells = sample_cells(dims, 48, seed=11)
+        cells[:, 2] = 0
+        lat.step(1)
+        check_sampled(lat, 2, dims, eq, 0, tau, 1, rho_fn, u_fn, 1, cells)
+        lat.step(1)
+        check_sampled(lat, 2, dims, eq, 0, tau, 1, rho_fn, u_fn, 2, cells)
+        lat.close()
+
+
+def test_batch_4096_sampled_instances():
+    from paper_2303_08163_gb300 import lbm
+    table = inputs.linear_mode_batch(count=4096, seed=2303)
+    count = len(table["nx"])
+    dims = np.stack([table["nx"], table["ny"], np.ones(count, dtype=np.int32)], axis=1)
+    fields = [inputs.linear_mode_fields(table, k) for k in range(count)]
+    rho = np.concatenate([f[0] for f in fields])
+    u = np.concatenate([f[1].reshape(-1) for f in fields])
+    kvec = np.stack([table["nmode"], np.zeros(count, np.int32), np.zeros(count, np.int32)], axis=1)
+    b = lbm.Batch(lbm.D2Q9, dims, table["tau"], core.EQ_ENTROPIC, 0)
+    b.init_fields(rho, u)
+    b.set_probe(kvec, 10)
+    steps = 61
+    b.step(steps)
+    series = b.probe_series()
+    pops = b.get_populations()
+    assert np.all(b.status() == 0)
+    ncells = dims.prod(axis=1)
+    order = np.argsort(ncells)
+    picks = list(order[:4]) + list(np.random.default_rng(1).choice(order[: count // 2], 4, replace=False))
+    for k in picks:
+        d3 = (int(dims[k, 0]), int(dims[k, 1]), 1)
+        f0 = core.init(2, d3, core.EQ_ENTROPIC, fields[k][0], fields[k][1])
+        fk, sk = core.run_probed(2, d3, core.EQ_ENTROPIC, 0, float(table["tau"][k]), steps, 10,
+                                 tuple(kvec[k]), f0)
+        c0, c1 = b.cell_start[k], b.cell_start[k + 1]
+        gk = pops[9 * c0: 9 * c1].reshape(9, -1)
+        assert float(np.max(np.abs(gk - fk) / np.abs(fk))) <= 1e-12
+        assert np.all(np.abs(series[k] - sk) <= 1e-12 * np.abs(sk) + 1e-13 * int(c1 - c0))
+    b.close()

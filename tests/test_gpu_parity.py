@@ -1,0 +1,307 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle, element by
+element on the same seeded inputs.
+
+Tolerances:
+- FP64 storage: max relative error per population <= 1e-12 (after up to 1000 steps).
+  Both sides evaluate the same formulas in IEEE FP64; they differ only by rounding
+  order (the GPU uses fused multiply-adds, 1/rho then a product, and the identity
+  (2 - S) Z = 2 S - 1 + 3u instead of the division by 1 - u), about 1e-16 per step.
+- FP32 storage of f - w rho0 with FP32 collision: relative L2 error of the velocity
+  field <= 1e-4, a tenth of the binary16 target (the FP32 collision arithmetic, a few
+  ulp of O(w) quantities per step, dominates the FP32 storage rounding).
+- binary16 storage with FP32 collision: relative L2 velocity error <= 1e-3 on
+  Taylor-Green (the target accuracy of the reduced-precision path).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import core
+from paper_2303_08163_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_library():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2303_08163_gb300 import build, lbm
+    build.build()
+    lbm.load()
+    yield
+
+
+def lbm_mod():
+    from paper_2303_08163_gb300 import lbm
+    return lbm
+
+
+def max_rel(a, b):
+    return float(np.max(np.abs(a - b) / np.abs(b)))
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run_gpu(D, dims, eq, bulk, tau, prec, rho, u, steps, shape=None, graph=False):
+    lbm = lbm_mod()
+    lat = lbm.Lattice(lbm.D2Q9 if D == 2 else lbm.D3Q27, dims, tau, eq, bulk, prec)
+    if shape is not None:
+        lat.set_launch_shape(*shape)
+    if graph:
+        lat.set_option(lbm.OPT_USE_GRAPH, 1)
+    lat.init_fields(rho, u)
+    lat.step(steps)
+    f = lat.get_populations()
+    info = lat.launch_info()
+    lat.close()
+    return f, info
+
+
+def run_oracle(D, dims, eq, bulk, tau, rho, u, steps):
+    return core.step(D, dims, eq, bulk, tau, steps, core.init(D, dims, eq, rho, u))
+
+
+# --------------------------------------------------------------------------- FP64 parity
+
+@pytest.mark.parametrize("kernel", ["generic", "tma"])
+def test_taylor_green_64_fp64_1000_steps(kernel):
+    """The small Taylor-Green configuration: D2Q9 64^2, u0 = 0.05, tau = 0.8, entropic,
+    FP64, 1000 steps (and one more, to check the odd-step layout)."""
+    lbm = lbm_mod()
+    n, tau = 64, 0.8
+    rho, u = inputs.taylor_green_2d(n, u0=0.05)
+    shape = (lbm.KERNEL_GENERIC, 256) if kernel == "generic" else (lbm.KERNEL_TMA, 256, 4, 4, n, 2048)
+    lat = lbm.Lattice(lbm.D2Q9, (n, n, 1), tau, lbm.ENTROPIC, 0, lbm.F64)
+    lat.set_launch_shape(*shape)
+    lat.init_fields(rho, u)
+    lat.step(1000)
+    ref = run_oracle(2, (n, n, 1), core.EQ_ENTROPIC, 0, tau, rho, u, 1000)
+    assert max_rel(lat.get_populations(), ref) <= 1e-12
+    lat.step(1)
+    ref1 = core.step(2, (n, n, 1), core.EQ_ENTROPIC, 0, tau, 1, ref)
+    assert lat.step_count == 1001
+    assert max_rel(lat.get_populations(), ref1) <= 1e-12
+    lat.close()
+
+
+# (D, dims, launch shape) covering: whole rows with several rows per job and y wrap,
+# aligned segments with halos and a shorter last segment, ragged Nx (generic only).
+SHAPES = [
+    (2, (40, 18, 1), (2, 256, 3, 4, 40, 2048)),
+    (2, (40, 18, 1), (2, 128, 2, 1, 16, 1024)),
+    (2, (13, 11, 1), (1, 128)),
+    (3, (12, 10, 6), (2, 128, 3, 3, 12, 1024)),
+    (3, (12, 10, 6), (2, 256, 2, 1, 4, 1024)),
+    (3, (7, 5, 6), (1, 256)),
+]
+
+
+@pytest.mark.parametrize("D,dims,shape", SHAPES)
+@pytest.mark.parametrize("eq", [core.EQ_ENTROPIC, core.EQ_POLY2, core.EQ_PRODUCT])
+@pytest.mark.parametrize("bulk", [0, 1])
+def test_fp64_parity_all_paths(D, dims, shape, eq, bulk):
+    """Every equilibrium, with and without the bulk correction, through every kernel
+    path, after an odd number of steps: max relative error per population <= 1e-12."""
+    rho, u = inputs.random_state(D, dims, seed=100 + 7 * eq + bulk + D, u_max=0.12)
+    steps, tau = 11, 0.57
+    got, info = run_gpu(D, dims, eq, bulk, tau, 0, rho, u, steps, shape=shape)
+    assert info["kernel"] == shape[0]
+    ref = run_oracle(D, dims, eq, bulk, tau, rho, u, steps)
+    assert max_rel(got, ref) <= 1e-12
+
+
+def test_init_and_moments_fp64():
+    """f = f^eq(rho, u) at t = 0 and the exported moments match the oracle."""
+    lbm = lbm_mod()
+    D, dims = 3, (8, 6, 5)
+    rho, u = inputs.random_state(D, dims, seed=3, u_max=0.3)
+    lat = lbm.Lattice(lbm.D3Q27, dims, 0.7, lbm.ENTROPIC, 0, lbm.F64)
+    lat.init_fields(rho, u)
+    assert max_rel(lat.get_populations(), core.init(D, dims, core.EQ_ENTROPIC, rho, u)) <= 1e-13
+    r, v = lat.moments()
+    np.testing.assert_allclose(r, rho, rtol=1e-14)
+    np.testing.assert_allclose(v, u, rtol=1e-12, atol=1e-15)
+    lat.close()
+
+
+# --------------------------------------------------------------------- reduced precision
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-4), (2, 1e-3)])
+def test_reduced_precision_taylor_green_2d(prec, tol):
+    """D2Q9 64^2 Taylor-Green, 500 steps: relative L2 velocity error against FP64."""
+    n, tau, steps = 64, 0.8, 500
+    rho, u = inputs.taylor_green_2d(n, u0=0.05)
+    got, _ = run_gpu(2, (n, n, 1), core.EQ_ENTROPIC, 0, tau, prec, rho, u, steps)
+    ref = run_oracle(2, (n, n, 1), core.EQ_ENTROPIC, 0, tau, rho, u, steps)
+    _, ug = core.moments(2, (n, n, 1), got)
+    _, ur = core.moments(2, (n, n, 1), ref)
+    err = rel_l2(ug, ur)
+    print(f"D2Q9 TGV {n}^2 prec={prec} steps={steps}: rel-L2 velocity error {err:.3e}")
+    assert err <= tol, f"rel-L2 velocity error {err:.3e} > {tol}"
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-4), (2, 1e-3)])
+@pytest.mark.parametrize("bulk", [0, 1])
+def test_reduced_precision_taylor_green_3d(prec, tol, bulk):
+    """D3Q27 32^3 Taylor-Green at Re = 1600 (u0 = 0.1, nu = u0 (N / 2 pi) / Re), four
+    convective times N / (2 pi u0): relative L2 velocity error against FP64."""
+    n, u0 = 32, 0.1
+    nu = u0 * (n / (2 * math.pi)) / 1600.0
+    tau = 0.5 + 3 * nu
+    steps = int(round(4 * n / (2 * math.pi * u0)))
+    rho, u = inputs.taylor_green_3d(n, u0=u0)
+    dims = (n, n, n)
+    got, _ = run_gpu(3, dims, core.EQ_ENTROPIC, bulk, tau, prec, rho, u, steps)
+    ref = run_oracle(3, dims, core.EQ_ENTROPIC, bulk, tau, rho, u, steps)
+    _, ug = core.moments(3, dims, got)
+    _, ur = core.moments(3, dims, ref)
+    err = rel_l2(ug, ur)
+    print(f"D3Q27 TGV {n}^3 prec={prec} bulk={bulk} steps={steps}: rel-L2 velocity error {err:.3e}")
+    assert err <= tol, f"rel-L2 velocity error {err:.3e} > {tol}"
+
+
+# ----------------------------------------------------------------------- diagnostics
+
+def test_fused_diagnostics_match_oracle():
+    lbm = lbm_mod()
+    n, tau = 48, 0.7
+    rho, u = inputs.taylor_green_2d(n, u0=0.08)
+    lat = lbm.Lattice(lbm.D2Q9, (n, n, 1), tau, lbm.ENTROPIC, 1, lbm.F64)
+    lat.set_option(lbm.OPT_DIAG_EVERY, 5)
+    lat.init_fields(rho, u)
+    lat.step(23)
+    hist = lat.diag_history()
+    assert [h["step"] for h in hist] == [0, 5, 10, 15, 20]
+    f = core.init(2, (n, n, 1), core.EQ_ENTROPIC, rho, u)
+    t = 0
+    for h in hist:
+        f = core.step(2, (n, n, 1), core.EQ_ENTROPIC, 1, tau, h["step"] - t, f)
+        t = h["step"]
+        d = core.diagnostics(2, (n, n, 1), f)
+        assert abs(h["mass"] - d["mass"]) <= 1e-12 * d["mass"]
+        np.testing.assert_allclose(h["momentum"], d["momentum"], atol=1e-12 * d["mass"])
+        assert abs(h["kinetic"] - d["kinetic"]) <= 1e-11 * d["kinetic"]
+        assert abs(h["max_u"] - d["max_u"]) <= 1e-13
+        assert h["nonfinite"] == 0
+    now = lat.diagnostics()
+    f = core.step(2, (n, n, 1), core.EQ_ENTROPIC, 1, tau, 23 - t, f)
+    d = core.diagnostics(2, (n, n, 1), f)
+    assert now["step"] == 23
+    assert abs(now["kinetic"] - d["kinetic"]) <= 1e-11 * d["kinetic"]
+    lat.close()
+
+
+def test_nonfinite_state_is_reported():
+    """A NaN population (fault injected on the host through lbm_set_populations) makes
+    the next fused diagnostics return LBM_ENONFINITE; the object stays usable."""
+    lbm = lbm_mod()
+    n = 16
+    rho, u = inputs.taylor_green_2d(n, u0=0.05)
+    lat = lbm.Lattice(lbm.D2Q9, (n, n, 1), 0.8, lbm.ENTROPIC, 0, lbm.F32)
+    lat.set_option(lbm.OPT_DIAG_EVERY, 1)
+    lat.init_fields(rho, u)
+    lat.step(3)
+    f = lat.get_populations()
+    f[4, 37] = np.nan
+    lat.set_populations(f)
+    with pytest.raises(lbm.LBMError) as e:
+        lat.step(2)
+    assert e.value.status == lbm.ENONFINITE
+    assert lat.diagnostics()["nonfinite"] >= 1
+    lat.close()
+
+
+# ------------------------------------------------------------ checkpoint, graph, self test
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_checkpoint_resume_is_bitwise(prec):
+    lbm = lbm_mod()
+    D, dims, tau = 3, (16, 12, 10), 0.6
+    rho, u = inputs.taylor_green_3d(16, u0=0.1)
+    rho, u = rho[: 16 * 12 * 10], u[:, : 16 * 12 * 10]
+    a = lbm.Lattice(lbm.D3Q27, dims, tau, lbm.ENTROPIC, 1, prec)
+    a.init_fields(rho, u)
+    a.step(14)
+    full = a.get_populations()
+    b = lbm.Lattice(lbm.D3Q27, dims, tau, lbm.ENTROPIC, 1, prec)
+    b.init_fields(rho, u)
+    b.step(7)
+    ck, t = b.get_populations("storage"), b.step_count
+    c = lbm.Lattice(lbm.D3Q27, dims, tau, lbm.ENTROPIC, 1, prec)
+    c.set_step_count(t)
+    c.set_populations(ck, "storage")
+    c.step(7)
+    np.testing.assert_array_equal(c.get_populations(), full)
+    np.testing.assert_array_equal(c.get_populations("storage"), a.get_populations("storage"))
+    for x in (a, b, c):
+        x.close()
+
+
+def test_graph_replay_equals_launches():
+    lbm = lbm_mod()
+    n = 64
+    rho, u = inputs.taylor_green_2d(n, u0=0.05)
+    f1, _ = run_gpu(2, (n, n, 1), 0, 0, 0.8, 1, rho, u, 41)
+    f2, _ = run_gpu(2, (n, n, 1), 0, 0, 0.8, 1, rho, u, 41, graph=True)
+    np.testing.assert_array_equal(f1, f2)
+
+
+def test_bounded_wait_times_out():
+    """A kernel waiting on a shared-memory barrier nothing arrives on returns
+    LBM_ETIMEOUT after its limit (1 ms) instead of hanging."""
+    lbm = lbm_mod()
+    assert lbm.selftest_bounded_wait(1_000_000) == lbm.ETIMEOUT
+
+
+def test_invalid_launch_shape_is_rejected():
+    lbm = lbm_mod()
+    lat = lbm.Lattice(lbm.D2Q9, (40, 8, 1), 0.8, lbm.ENTROPIC, 0, lbm.F32)
+    with pytest.raises(lbm.LBMError):
+        lat.set_launch_shape(2, 256, 3, 1, 6, 1024)  # segment not a multiple of 4 floats
+    with pytest.raises(lbm.LBMError):
+        lat.set_launch_shape(2, 256, 9, 1, 40, 1024)  # too many stages
+    lat.close()
+    lat = lbm.Lattice(lbm.D2Q9, (13, 8, 1), 0.8, lbm.ENTROPIC, 0, lbm.F32)
+    assert lat.launch_info()["kernel"] == lbm.KERNEL_GENERIC  # 52-byte rows: no TMA
+    with pytest.raises(lbm.LBMError):
+        lat.set_launch_shape(2, 256, 3, 1, 13, 1024)
+    lat.close()
+
+
+# ------------------------------------------------------------------------------- batch
+
+def test_batch_parity_and_probes():
+    """Batched FP64 instances of ragged sizes and per-instance tau: populations after an
+    odd number of steps and the probe series equal the oracle's instance by instance."""
+    lbm = lbm_mod()
+    table = inputs.linear_mode_batch(count=12, seed=7, nmin=5, nmax=40)
+    dims = np.stack([table["nx"], table["ny"], np.ones(12, dtype=np.int32)], axis=1)
+    fields = [inputs.linear_mode_fields(table, k) for k in range(12)]
+    rho = np.concatenate([f[0] for f in fields])
+    u = np.concatenate([f[1].reshape(-1) for f in fields])
+    kvec = np.stack([table["nmode"], np.zeros(12, dtype=np.int32), np.zeros(12, dtype=np.int32)], axis=1)
+    for eq, bulk in ((core.EQ_ENTROPIC, 0), (core.EQ_POLY2, 1)):
+        b = lbm.Batch(lbm.D2Q9, dims, table["tau"], eq, bulk)
+        b.init_fields(rho, u)
+        b.set_probe(kvec, 3)
+        b.step(20)
+        b.step(11)
+        series = b.probe_series()
+        pops = b.get_populations()
+        assert series.shape == (12, 11, 4)
+        assert np.all(b.status() == 0)
+        for k in range(12):
+            d3 = (int(dims[k, 0]), int(dims[k, 1]), 1)
+            f0 = core.init(2, d3, eq, fields[k][0], fields[k][1])
+            fk, sk = core.run_probed(2, d3, eq, bulk, float(table["tau"][k]), 31, 3, tuple(kvec[k]), f0)
+            c0, c1 = b.cell_start[k], b.cell_start[k + 1]
+            gk = pops[9 * c0: 9 * c1].reshape(9, -1)
+            assert max_rel(gk, fk) <= 1e-12
+            # each projection sums ncell terms of order one: absolute floor ncell * 1e-13
+            ncell = int(c1 - c0)
+            assert np.all(np.abs(series[k] - sk) <= 1e-12 * np.abs(sk) + 1e-13 * ncell)
+        b.close()
