@@ -182,6 +182,12 @@ def ncu_traffic(kernel, workload_name, ncell):
     return None
 
 
+def aggregate(world, cells_per_rank, steps, rank_ms):
+    """Whole-job GLUPS: every rank advances its own replica; the slowest rank's time
+    bounds the job (weak scaling)."""
+    return world * cells_per_rank * steps / (max(rank_ms) * 1e-3) / 1e9
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
@@ -359,7 +365,7 @@ def run_native(args):
     info = lat.launch_info()
     kname = "k_step_tma" if info["kernel"] == 2 else "k_step_generic"
     traffic = ncu_traffic(kname, w["name"], ncell)
-    glups = ws * ncell * args.steps / (t_max * 1e-3) / 1e9
+    glups = aggregate(ws, ncell, args.steps, [t_max])
     # end to end through the C ABI with pinned host buffers
     rho_h = rho.cpu().pin_memory()
     u_h = u.cpu().pin_memory()

@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(256) k_step_generic(const lbmh::StepArgs a) {
     const int nx = a.lat.nx, ny = a.lat.ny, nz = a.lat.nz;
     const R rho0 = R(a.rho0), omega0 = R(a.omega0), six_nu = R(a.six_nu);
     DiagAcc acc;
+    DiagLocal<R> loc;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const bool small = a.lat.ncell < ((int64_t)1 << 31);
     for (int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; cell < a.lat.ncell;
@@ -87,9 +88,15 @@ __global__ void __launch_bounds__(256) k_step_generic(const lbmh::StepArgs a) {
         }
         const CellMoments<R> m = aa_cell_step<D, P, EQ, BULK>(A, a.lat.plane, nx, ny, nz, x, y, z,
                                                               a.odd, rho0, omega0, six_nu);
-        if (a.diag) acc.add(m.rho, m.u);
+        if (a.diag) {
+            loc.add(m.rho, m.u, rho0);
+            if (loc.count == 16) loc.flush(acc, a.rho0);
+        }
     }
-    if (a.diag) diag_block_store(acc, a.partials + (int64_t)blockIdx.x * lbmh::kDiagWords);
+    if (a.diag) {
+        loc.flush(acc, a.rho0);
+        diag_block_store(acc, a.partials + (int64_t)blockIdx.x * lbmh::kDiagWords);
+    }
 }
 
 template <int D, int P>

@@ -178,6 +178,7 @@ __device__ __forceinline__ void tma_compute(const lbmh::StepArgs &a, const TmaGe
     const R rho0 = R(a.rho0), omega0 = R(a.omega0), six_nu = R(a.six_nu);
     const bool whole = g.nseg == 1;
     const int ncells = j.nrows * j.len;
+    DiagLocal<R> loc;
     // cell c of the job: row r = c / len, xl = c % len, advanced incrementally
     int r = tid / j.len;
     int xl = tid - r * j.len;
@@ -210,13 +211,14 @@ __device__ __forceinline__ void tma_compute(const lbmh::StepArgs &a, const TmaGe
                 row[(Q - 1 - i) * bs + p] = St::store(f[i]);
             }
         }
-        if (a.diag) acc.add(m.rho, m.u);
+        if (a.diag) loc.add(m.rho, m.u, rho0);
         xl += nthr;
         while (xl >= j.len) {
             xl -= j.len;
             ++r;
         }
     }
+    if (a.diag) loc.flush(acc, a.rho0);
 }
 
 template <int D, int P, int EQ, bool BULK, int CAPB>

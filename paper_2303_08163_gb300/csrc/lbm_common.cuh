@@ -50,6 +50,39 @@ struct DiagAcc {
     }
 };
 
+// Partial diagnostics of a few cells in the collision precision R, flushed into the FP64
+// accumulator once per job (FP64 arithmetic is a small fraction of the FP32 rate on
+// this GPU, so per-cell FP64 sums would dominate a diagnostics step).  Mass is summed as
+// rho - rho0 so the FP32 partials carry only the small deviations.
+template <typename R>
+struct DiagLocal {
+    R dm = 0, jx = 0, jy = 0, jz = 0, ke = 0, umax = 0;
+    int nf = 0, count = 0;
+
+    __device__ __forceinline__ void add(R rho, const R (&u)[3], R rho0) {
+        const bool fin = isfinite(rho) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]);
+        nf += fin ? 0 : 1;
+        ++count;
+        dm += rho - rho0;
+        jx += rho * u[0];
+        jy += rho * u[1];
+        jz += rho * u[2];
+        ke += R(0.5) * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        umax = fmax(umax, fmax(fabs(u[0]), fmax(fabs(u[1]), fabs(u[2]))));
+    }
+
+    __device__ __forceinline__ void flush(DiagAcc &acc, double rho0) {
+        acc.m += (double)count * rho0 + (double)dm;
+        acc.jx += (double)jx;
+        acc.jy += (double)jy;
+        acc.jz += (double)jz;
+        acc.ke += (double)ke;
+        acc.umax = fmax(acc.umax, (double)umax);
+        acc.nf += (double)nf;
+        *this = DiagLocal<R>();
+    }
+};
+
 __device__ __forceinline__ double shfl_down_d(double v, int off) {
     return __shfl_down_sync(0xffffffffu, v, off);
 }

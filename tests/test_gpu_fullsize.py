@@ -84,12 +84,18 @@ def test_tgv_512_sampled_and_conservation(prec):
     lat.step(1)
     check_sampled(lat, 3, dims, core.EQ_ENTROPIC, 0, tau, prec, rho_fn, u_fn, 2, cells)
     d0 = lat.diagnostics()
-    lat.step(40)
+    nsteps = 40
+    lat.step(nsteps)
     d1 = lat.diagnostics()
     assert d1["nonfinite"] == 0
-    rel = 1e-6 if prec == 2 else 1e-9
-    assert abs(d1["mass"] - d0["mass"]) <= rel * d0["mass"]
-    assert np.all(np.abs(d1["momentum"] - d0["momentum"]) <= rel * d0["mass"])
+    # Conservation to round-off: every step rounds each stored f - w rho0 once (unit u of
+    # the storage format) and the FP32 collision adds a few ulp; sum |f - w rho0| over a
+    # cell is below 0.3 rho for |u| <= 0.1, so |d mass| <= steps * 2u * 0.3 * mass.
+    bound = nsteps * 2 * UNIT[prec] * 0.3 * d0["mass"]
+    drift = abs(d1["mass"] - d0["mass"])
+    print(f"prec={prec}: mass drift {drift:.3e} over {nsteps} steps (bound {bound:.3e})")
+    assert drift <= bound
+    assert np.all(np.abs(d1["momentum"] - d0["momentum"]) <= bound)
     lat.close()
     del rho, u
     torch.cuda.empty_cache()
