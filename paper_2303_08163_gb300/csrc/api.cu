@@ -157,6 +157,9 @@ StepArgs step_args(lbm_ctx *c, int odd, int diag) {
     a.rho0 = c->rho0;
     a.omega0 = c->omega0;
     a.six_nu = c->six_nu;
+    a.rho0f = (float)c->rho0;
+    a.omega0f = (float)c->omega0;
+    a.six_nuf = (float)c->six_nu;
     a.odd = odd;
     a.diag = diag;
     a.partials = c->partials;

@@ -65,7 +65,8 @@ __global__ void __launch_bounds__(256) k_step_generic(const lbmh::StepArgs a) {
     using R = typename St::R;
     T *__restrict__ A = static_cast<T *>(a.lat.A);
     const int nx = a.lat.nx, ny = a.lat.ny, nz = a.lat.nz;
-    const R rho0 = R(a.rho0), omega0 = R(a.omega0), six_nu = R(a.six_nu);
+    const R rho0 = step_scalar<R>(a.rho0, a.rho0f), omega0 = step_scalar<R>(a.omega0, a.omega0f),
+            six_nu = step_scalar<R>(a.six_nu, a.six_nuf);
     DiagAcc acc;
     DiagLocal<R> loc;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;

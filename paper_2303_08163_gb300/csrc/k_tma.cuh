@@ -175,7 +175,8 @@ __device__ __forceinline__ void tma_compute(const lbmh::StepArgs &a, const TmaGe
     using R = typename St::R;
     constexpr int Q = qof(D);
     constexpr int bs = CAPB / (int)sizeof(T);  // compile-time offsets between buffers
-    const R rho0 = R(a.rho0), omega0 = R(a.omega0), six_nu = R(a.six_nu);
+    const R rho0 = step_scalar<R>(a.rho0, a.rho0f), omega0 = step_scalar<R>(a.omega0, a.omega0f),
+            six_nu = step_scalar<R>(a.six_nu, a.six_nuf);
     const bool whole = g.nseg == 1;
     const int ncells = j.nrows * j.len;
     DiagLocal<R> loc;

@@ -9,6 +9,11 @@ namespace lbmd {
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
+// A per-step scalar in the collision precision (no FP64 conversion in FP32 kernels).
+template <typename R> __device__ __forceinline__ R step_scalar(double d, float f);
+template <> __device__ __forceinline__ double step_scalar<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float step_scalar<float>(double, float f) { return f; }
+
 // Canonical population f_i(r) = A[i][r] after an even number of steps and
 // A[opp(i)][r - c_i] after an odd number (AA pattern: the odd step leaves post-collision
 // values in the opposite slot of the sending cell).

@@ -240,6 +240,9 @@ __host__ __device__ __forceinline__ CellMoments<R> moments_shifted(const R (&f)[
 template <int D, int EQ, bool BULK, typename R>
 __host__ __device__ __forceinline__ CellMoments<R> collide(R (&f)[qof(D)], R rho0, R omega0, R six_nu) {
     constexpr int Q = qof(D);
+    // weights per number of nonzero velocity components, folded at compile time
+    constexpr double kW0 = wclass_weight<D>(0), kW1 = wclass_weight<D>(1);
+    constexpr double kW2 = wclass_weight<D>(2), kW3 = wclass_weight<D>(D >= 3 ? 3 : 0);
     const CellMoments<R> m = moments_shifted<D, R>(f, rho0);
     const R drho = m.rho - rho0;
     if constexpr (EQ == EQ_POLY2) {
@@ -250,9 +253,7 @@ __host__ __device__ __forceinline__ CellMoments<R> collide(R (&f)[qof(D)], R rho
         const R om = collision_rate<EQ, BULK, R>(k, omega0, six_nu);
         const R keep = R(1) - om;
         const R mh = R(-1.5) * uu;
-        R omw[4];
-#pragma unroll
-        for (int c = 0; c <= D; ++c) omw[c] = om * R(wclass_weight<D>(c));
+        const R omw[4] = {om * R(kW0), om * R(kW1), om * R(kW2), om * R(kW3)};
         const R upm = m.u[0] + m.u[1], umm = m.u[0] - m.u[1];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -276,9 +277,7 @@ __host__ __device__ __forceinline__ CellMoments<R> collide(R (&f)[qof(D)], R rho
         if constexpr (D == 3) kmax = fmax(kmax, key[2]);
         const R om = collision_rate<EQ, BULK, R>(kmax, omega0, six_nu);
         const R keep = R(1) - om;
-        R omw[4];
-#pragma unroll
-        for (int c = 0; c <= D; ++c) omw[c] = om * R(wclass_weight<D>(c));
+        const R omw[4] = {om * R(kW0), om * R(kW1), om * R(kW2), om * R(kW3)};
         const R dx[3] = {dm[0], d0[0], dp[0]};
         const R dy[3] = {dm[1], d0[1], dp[1]};
         const R tx[3] = {R(1) + dm[0], R(1) + d0[0], R(1) + dp[0]};

@@ -22,6 +22,7 @@ struct StepArgs {
     Lattice lat;
     int eq, bulk;
     double rho0, omega0, six_nu;  // reference density, 1/tau, 6 nu
+    float rho0f, omega0f, six_nuf; // the same in single precision (FP32 collisions)
     int odd;                      // AA pattern: 0 = even step, 1 = odd step
     int diag;                     // 1 = reduce diagnostics into partials
     double *partials;             // [blocks][8] when diag

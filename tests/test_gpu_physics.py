@@ -1,0 +1,134 @@
+"""Physics pins of the CUDA path (through the C ABI), against closed forms of the paper and
+the von Neumann eigenvalues of the oracle's discrete scheme.
+
+* The small Taylor-Green configuration (D2Q9 64^2, u0 = 0.05, tau = 0.8, FP64): the
+  kinetic energy from the fused diagnostics decays at 2 nu (k_x^2 + k_y^2),
+  nu = (tau - 1/2)/3, within 1 %.
+* Batched linear modes: the per-step multipliers fitted from the probe series (dynamic
+  mode decomposition) equal the eigenvalues of M = E (delta + J) (Eq. eq:VN_eigen) of the
+  hydrodynamic modes.
+* The paper's pressure-wave experiment (Sec. V.B.2): a 1-D wave rho = 1 + drho sin(2 pi x / N)
+  on a uniform flow U0, nu = 0.05, entropic and product-form equilibria with and
+  without the corrected relaxation rate; the effective viscosity fitted from the energy
+  decay equals the von Neumann prediction, the correction brings it closer to nu, and
+  the uncorrected product form deviates more than the uncorrected entropic form.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import analysis, core
+from paper_2303_08163_gb300 import fits, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda_library():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2303_08163_gb300 import build, lbm
+    build.build()
+    lbm.load()
+    yield
+
+
+def test_taylor_green_64_energy_decay_rate():
+    from paper_2303_08163_gb300 import lbm
+    n, tau = 64, 0.8
+    nu = (tau - 0.5) / 3.0
+    rho, u = inputs.taylor_green_2d(n, u0=0.05)
+    lat = lbm.Lattice(lbm.D2Q9, (n, n, 1), tau, lbm.ENTROPIC, 0, lbm.F64)
+    lat.set_option(lbm.OPT_DIAG_EVERY, 50)
+    lat.init_fields(rho, u)
+    lat.step(1000)
+    hist = lat.diag_history()
+    t = np.array([h["step"] for h in hist], dtype=float)
+    e = np.array([h["kinetic"] for h in hist])
+    rate = fits.energy_decay_rate(t, e, skip=2)
+    k = 2 * math.pi / n
+    expect = 2 * nu * (k * k + k * k)
+    print(f"TGV 64^2: fitted energy decay {rate:.6e} per step, 2 nu (kx^2 + ky^2) = {expect:.6e}")
+    assert abs(rate / expect - 1) < 0.01
+    lat.close()
+
+
+def _batch(lbm, table, eq, bulk, every_k, steps):
+    count = len(table["nx"])
+    dims = np.stack([table["nx"], table["ny"], np.ones(count, dtype=np.int32)], axis=1)
+    fields = [inputs.linear_mode_fields(table, k) for k in range(count)]
+    rho = np.concatenate([f[0] for f in fields])
+    u = np.concatenate([f[1].reshape(-1) for f in fields])
+    kvec = np.stack([table["nmode"], np.zeros(count, np.int32), np.zeros(count, np.int32)], axis=1)
+    b = lbm.Batch(lbm.D2Q9, dims, table["tau"], eq, bulk)
+    b.init_fields(rho, u)
+    b.set_probe(kvec, every_k)
+    b.step(steps)
+    s = b.probe_series()
+    b.close()
+    return s
+
+
+@pytest.mark.parametrize("eq", [core.EQ_ENTROPIC, core.EQ_POLY2])
+def test_batched_modes_match_von_neumann(eq):
+    """Shear and acoustic waves on background flows: fitted multipliers = eigenvalues."""
+    from paper_2303_08163_gb300 import lbm
+    rng = np.random.default_rng(9)
+    count = 12
+    table = {"nx": np.full(count, 64, np.int32), "ny": np.full(count, 4, np.int32),
+             "nmode": rng.integers(1, 4, count).astype(np.int32),
+             "U0": rng.uniform(0.0, 0.25, count), "tau": 0.5 + rng.uniform(0.05, 0.5, count),
+             "kind": np.arange(count, dtype=np.int32) % 2, "amp": 1e-5}
+    every_k, steps = 2, 1200
+    s = _batch(lbm, table, eq, 0, every_k, steps)
+    for i in range(count):
+        k = 2 * math.pi * table["nmode"][i] / 64
+        U0 = float(table["U0"][i])
+        lam_vn, vec = analysis.hydrodynamic_modes(2, eq, 0, float(table["tau"][i]), 1.0, [U0, 0.0], [k, 0.0])
+        c, _ = core.lattice(2)
+        series = s[i, 100:]  # after the non-hydrodynamic transients
+        if table["kind"][i] == 0:
+            sel = [int(np.argmax(np.abs(c[:, 1] @ vec)))]
+            mu = fits.mode_multipliers(series[:, 2], nmodes=1)
+        else:
+            sel = [j for j in range(3) if j != int(np.argmax(np.abs(c[:, 1] @ vec)))]
+            mu = fits.mode_multipliers(series[:, :2], nmodes=2)
+        target = np.array(lam_vn)[sel] ** every_k
+        for m in mu:
+            assert np.min(np.abs(target - m)) < 2e-6, (i, m, target)
+
+
+def test_paper_pressure_wave_experiment():
+    """Sec. V.B.2: effective viscosity vs U0 from the energy decay of a 1-D pressure wave."""
+    from paper_2303_08163_gb300 import lbm
+    nx, nu = 128, 0.05
+    tau = 0.5 + 3 * nu
+    k = 2 * math.pi / nx
+    U0s = [0.0, 0.1, 0.2, 0.3]
+    rows = []
+    nu_eff = {}
+    for eq in (core.EQ_ENTROPIC, core.EQ_PRODUCT):
+        for bulk in (0, 1):
+            count = len(U0s)
+            table = {"nx": np.full(count, nx, np.int32), "ny": np.ones(count, np.int32),
+                     "nmode": np.ones(count, np.int32), "U0": np.array(U0s), "tau": np.full(count, tau),
+                     "kind": np.ones(count, np.int32), "amp": 1e-4}
+            s = _batch(lbm, table, eq, bulk, 1, 4000)
+            for i, U0 in enumerate(U0s):
+                rho_h, jx_h = s[i, :, 0], s[i, :, 1]
+                # E = sum 1/2 |j - U0 rho|^2 + vs^2 rho'^2 / 2 of the single mode (Parseval)
+                energy = 0.5 * np.abs(jx_h - U0 * rho_h) ** 2 + 0.5 / 3.0 * np.abs(rho_h) ** 2
+                rate = fits.energy_decay_rate(np.arange(len(energy)), energy, skip=200)
+                lam, _ = analysis.hydrodynamic_modes(1, eq, bulk, tau, 1.0, [U0], [k])
+                vn = float(np.mean(-np.log(np.abs(lam))))  # two acoustic modes, equal weight
+                nu_eff[(eq, bulk, U0)] = rate / (2 * k * k)
+                rows.append((eq, bulk, U0, rate / (2 * k * k), vn / (k * k)))
+                assert abs(rate / 2 - vn) <= 0.02 * vn
+    print("eq bulk U0 nu_eff(fit) nu_eff(von Neumann)")
+    for r in rows:
+        print(f"{r[0]} {r[1]} {r[2]:.1f} {r[3]:.5f} {r[4]:.5f}")
+    for U0 in (0.2, 0.3):
+        for eq in (core.EQ_ENTROPIC, core.EQ_PRODUCT):
+            assert abs(nu_eff[(eq, 1, U0)] - nu) < abs(nu_eff[(eq, 0, U0)] - nu)
+        assert abs(nu_eff[(core.EQ_PRODUCT, 0, U0)] - nu) > abs(nu_eff[(core.EQ_ENTROPIC, 0, U0)] - nu)
