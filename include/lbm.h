@@ -271,6 +271,31 @@ void lbm_batch_destroy(lbm_batch *b);
 /* Message of the last failed call on this host thread ("" if none). */
 const char *lbm_last_error(void);
 
+/*
+ * Global diagnostics of populations the caller owns, computed without allocating any
+ * device memory.  The paper has no counterpart: this is a utility for callers that
+ * cannot call cudaMalloc (code running inside another framework's memory pool, programs
+ * that reserve all device memory up front, or work recorded inside a stream capture).
+ *   lattice  LBM_D2Q9 (dims[2] == 1) or LBM_D3Q27.
+ *   f        device pointer to canonical FP64 populations f[Q][ncell] (not shifted;
+ *            population and cell order as above), read only.
+ *   blocks   number of per-block partial sums, 1 <= blocks <= 1024.  The partial sums
+ *            live in one static device array of 1024 records (64 KiB), which every
+ *            device that loads the library holds until the process exits; larger values
+ *            return LBM_EINVAL.
+ *   out      device pointer to 8 doubles written on the stream: mass, momentum[3],
+ *            kinetic, max |u_a|, number of non-finite cells, 0.
+ *   cuda_stream  the stream the two kernels are ordered on (NULL = legacy stream).
+ * The call does not synchronise.  Its first call on a device looks up the static
+ * array's device address for that device (the device current at the call), so make the
+ * first call on each device before any stream capture.  All calls share the one static
+ * array: calls whose kernels overlap on the GPU (different streams, or host threads
+ * without ordering between them) race and corrupt each other's results; order them on
+ * one stream.  Every call rewrites the records it reads, so no clearing is needed.
+ */
+int lbm_diagnostics_noalloc(int lattice, const int64_t dims[3], const double *f, int64_t blocks,
+                            double *out, void *cuda_stream);
+
 /* Library version as major * 10000 + minor * 100 + patch. */
 int lbm_version(void);
 

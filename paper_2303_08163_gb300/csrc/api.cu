@@ -435,6 +435,13 @@ int autotune(lbm_ctx *c) {
 
 }  // namespace
 
+namespace lbmh {
+int set_last_error(int code, const char *msg) {
+    g_err = msg;
+    return code;
+}
+}  // namespace lbmh
+
 extern "C" {
 
 const char *lbm_last_error(void) { return g_err.c_str(); }

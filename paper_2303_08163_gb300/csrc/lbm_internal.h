@@ -44,6 +44,9 @@ struct TmaShape {
 constexpr int kDiagWords = 8;  // mass, jx, jy, jz, kinetic, max|u|, nonfinite, unused
 constexpr int kTmaMaxStages = 8;  // deepest shared-memory pipeline of the TMA row kernel
 
+// api.cu: record the message of a failed call for lbm_last_error(); returns code.
+int set_last_error(int code, const char *msg);
+
 // k_generic.cu
 cudaError_t step_generic(const StepArgs &a, int blocks, int threads, cudaStream_t s);
 cudaError_t init_fields(const Lattice &lat, int eq, double rho0, const void *rho, const void *u,

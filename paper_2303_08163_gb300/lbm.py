@@ -72,6 +72,7 @@ SIGNATURES = {
     "lbm_last_error": (ctypes.c_char_p, []),
     "lbm_version": (_i, []),
     "lbm_selftest_bounded_wait": (_i, [_vp, _i64, _pi32]),
+    "lbm_diagnostics_noalloc": (_i, [_i, _p64, _vp, _i64, _vp, _vp]),
 }
 
 _lib = None
@@ -351,6 +352,14 @@ class Batch:
 
     def sync(self):
         _check(load().lbm_batch_sync(self._h))
+
+
+def diagnostics_noalloc(lattice, dims, f, out, blocks=256, stream=None):
+    """lbm_diagnostics_noalloc on device tensors: f (Q, ncell) float64 canonical
+    populations, out (8,) float64; nothing is allocated and nothing synchronised."""
+    d = (ctypes.c_int64 * 3)(*(list(dims) + [1, 1, 1])[:3])
+    _check(load().lbm_diagnostics_noalloc(int(lattice), d, ctypes.c_void_p(f.data_ptr()), int(blocks),
+                                          ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
 
 
 def selftest_bounded_wait(timeout_ns=1_000_000, stream=None):
