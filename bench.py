@@ -41,7 +41,7 @@ def parse():
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
-    p.add_argument("--workload", default="tgv3d", choices=["tgv3d", "shear2d", "tgv2d", "batch"])
+    p.add_argument("--workload", default="tgv3d", choices=["tgv3d", "shear2d", "tgv2d", "batch", "turb3d"])
     p.add_argument("--precision", default=None, choices=list(PREC))
     p.add_argument("--bulk", type=int, default=0)
     p.add_argument("--eq", default="entropic", choices=["entropic", "poly2", "product"])
@@ -67,6 +67,12 @@ def workload(args):
         prec = PREC[args.precision or "f16s"]
         return dict(name=f"D3Q27 {n}^3 periodic Taylor-Green vortex (u0=0.1, rho0=1, Re=1600)",
                     D=3, dims=(n, n, n), tau=0.5 + 3 * nu, prec=prec, eq=eq, u0=u0)
+    if args.workload == "turb3d":
+        n = args.n or 512
+        prec = PREC[args.precision or "f16s"]
+        return dict(name=f"D3Q27 {2 * n}x{n}x{n} periodic decaying isotropic turbulence "
+                         f"(E(k) ~ k^4 exp(-2 (k/8)^2), u_rms=0.05)",
+                    D=3, dims=(2 * n, n, n), tau=0.5 + 1e-4, prec=prec, eq=eq, u0=0.05)
     if args.workload == "shear2d":
         n = args.n or 4096
         prec = PREC[args.precision or "f32"]
@@ -85,6 +91,9 @@ def workload(args):
 def fields_device(w, torch, dev):
     """Initial fields as float32 device tensors (flat rho, u[D][ncell])."""
     D, (nx, ny, nz) = w["D"], w["dims"]
+    if "turbulence" in w["name"]:
+        from paper_2303_08163_gb300 import inputs
+        return inputs.random_solenoidal_torch((nx, ny, nz), u_rms=0.05, device=dev)
     if w["name"].startswith("D3Q27"):
         n = nx
         t = torch.arange(n, device=dev, dtype=torch.float64) * (2 * math.pi / n)
@@ -399,7 +408,9 @@ def run_native(args):
         del lat
         torch.cuda.empty_cache()
         extras["precision_compare"] = compare_precisions(torch, lbm, dev, w, args, rho, u)
-        if w["D"] == 3:
+        if "turbulence" in w["name"]:
+            extras["energy_decay"] = energy_decay_compare(torch, lbm, w, args, rho, u)
+        elif w["D"] == 3:
             extras["l2_velocity_error"] = velocity_error(torch, lbm, dev)
     cpu = None
     if rank == 0:
@@ -426,6 +437,36 @@ def run_native(args):
     }
     line.update(extras)
     print(json.dumps(line), flush=True)
+
+
+def energy_decay_compare(torch, lbm, w, args, rho, u, steps=5000, every=100):
+    """Kinetic-energy decay of the binary16 run against the FP32 run (fused diagnostics
+    every `every` steps): the largest relative difference of E(t) over the steps both runs
+    stayed finite, and the step at which each run first became non-finite (None if not)."""
+    curves, diverged = {}, {}
+    for prec in (2, 1):
+        lat = lbm.Lattice(lbm.D3Q27, w["dims"], w["tau"], w["eq"], 0, prec)
+        lat.init_fields(rho, u, dtype=np.float32)
+        lat.set_option(lbm.OPT_DIAG_EVERY, every)
+        diverged[prec] = None
+        try:
+            lat.step(steps + 1)
+        except lbm.LBMError as e:
+            if e.status != lbm.ENONFINITE:
+                raise
+        hist = lat.diag_history()
+        bad = [h["step"] for h in hist if h["nonfinite"] > 0 or not np.isfinite(h["kinetic"])]
+        diverged[prec] = bad[0] if bad else None
+        curves[prec] = {h["step"]: h["kinetic"] for h in hist if h["nonfinite"] == 0 and np.isfinite(h["kinetic"])}
+        lat.close()
+        torch.cuda.empty_cache()
+    common = sorted(set(curves[2]) & set(curves[1]))
+    rel = [abs(curves[2][t] - curves[1][t]) / curves[1][t] for t in common]
+    return {"steps": steps, "every": every, "compared_until": common[-1] if common else None,
+            "max_rel_diff": max(rel) if rel else None,
+            "E_last_over_E0": curves[1][common[-1]] / curves[1][common[0]] if common else None,
+            "nonfinite_from_step": {"F16S": diverged[2], "F32": diverged[1]},
+            "note": "constant-tau BGK at tau - 1/2 = 1e-4 without a nonlinear limiter"}
 
 
 def compare_precisions(torch, lbm, dev, w, args, rho, u):

@@ -265,6 +265,36 @@ int lbm_batch_sync(lbm_batch *b);
 void lbm_batch_destroy(lbm_batch *b);
 
 /* ------------------------------------------------------------------------------------
+ * Linear stability (von Neumann analysis of the D2Q9 scheme, Sec. V.A)
+ * ------------------------------------------------------------------------------------ */
+
+/*
+ * Eigenvalues of the amplification matrix M = E (delta + J) of Eq. (eq:VN_eigen) for count
+ * parameter points, computed on the GPU in FP64 (one point per thread).  J = 2 beta
+ * (d f^eq / d f - I) is the Jacobian of the collision operator at f = f^eq(rho, u), with
+ * the exact derivatives of the eq_kind equilibrium; E_ij = exp(-i c_i . k) delta_ij.
+ * With bulk_corr = 1, 2 beta is the corrected rate of Eq. (eq:redefined_relaxation rate)
+ * at u.  params: host [count][6] = {tau, rho, u_x, u_y, k_x, k_y}; out: host
+ * [count][9][2] (re, im), each point's eigenvalues sorted by decreasing modulus.  A mode
+ * exp(i (k.r - Omega t)) has lambda = exp(-i Omega): decay -ln|lambda| per step, phase
+ * speed -arg(lambda) / |k|.  Synchronises.  LBM_ECUDA also when the QR iteration of some
+ * point did not converge.
+ */
+int lbm_vn_eigenvalues(int eq_kind, int bulk_corr, int64_t count, const double *params, double *out,
+                       void *cuda_stream);
+
+/*
+ * Linear-stability limit of Sec. V.A.2: for each of npairs (nu, theta) pairs, the largest
+ * speed |u| in [0, u_hi] such that every eigenvalue of M has modulus <= 1 + tol for all
+ * wave vectors of an nk x nk grid of [0, pi]^2, with u = |u| (cos theta, sin theta),
+ * rho = 1 and tau = 1/2 + 3 nu (constant relaxation).  Found by `iterations` bisection
+ * steps (stability is taken to hold below the limit); umax: host [npairs].
+ * nu, theta: host [npairs].  Synchronises.
+ */
+int lbm_vn_stability_limit(int eq_kind, int64_t npairs, const double *nu, const double *theta, int nk,
+                           double u_hi, int iterations, double tol, double *umax, void *cuda_stream);
+
+/* ------------------------------------------------------------------------------------
  * Library
  * ------------------------------------------------------------------------------------ */
 

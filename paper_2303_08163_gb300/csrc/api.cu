@@ -878,6 +878,103 @@ void lbm_destroy(lbm_ctx *c) {
     delete c;
 }
 
+// ------------------------------------------------------------------- von Neumann analysis
+
+namespace {
+// Device buffers of one von Neumann call, freed on every return path.
+struct VnBufs {
+    void *p[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    ~VnBufs() {
+        for (void *q : p)
+            if (q) cudaFree(q);
+    }
+    bool alloc(int i, size_t bytes) {
+        if (cudaMalloc(&p[i], bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return true;
+    }
+};
+}  // namespace
+
+int lbm_vn_eigenvalues(int eq_kind, int bulk_corr, int64_t count, const double *params, double *out,
+                       void *cuda_stream) {
+    if (eq_kind < 0 || eq_kind > 2 || (bulk_corr != 0 && bulk_corr != 1) || count < 0 ||
+        (count > 0 && (!params || !out)))
+        return fail(LBM_EINVAL, "bad von Neumann arguments");
+    if (count == 0) return LBM_OK;
+    for (int64_t p = 0; p < count; ++p)
+        if (!(params[6 * p] > 0.5) || !(params[6 * p + 1] > 0))
+            return fail(LBM_EINVAL, "point %lld: tau must be > 1/2 and rho > 0", (long long)p);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    VnBufs b;
+    if (!b.alloc(0, sizeof(double) * 6 * count) || !b.alloc(1, sizeof(double) * 18 * count) ||
+        !b.alloc(2, sizeof(int32_t)))
+        return fail(LBM_ENOMEM, "von Neumann buffers");
+    CK(cudaMemcpyAsync(b.p[0], params, sizeof(double) * 6 * count, cudaMemcpyHostToDevice, s), "params upload");
+    CK(cudaMemsetAsync(b.p[2], 0, sizeof(int32_t), s), "status clear");
+    CK(vn_eigs(eq_kind, bulk_corr, count, (const double *)b.p[0], (double *)b.p[1], (int32_t *)b.p[2], s),
+       "eigenvalue kernel");
+    int32_t st = 0;
+    CK(cudaMemcpyAsync(out, b.p[1], sizeof(double) * 18 * count, cudaMemcpyDeviceToHost, s), "eigenvalue copy");
+    CK(cudaMemcpyAsync(&st, b.p[2], sizeof(int32_t), cudaMemcpyDeviceToHost, s), "status copy");
+    CK(cudaStreamSynchronize(s), "eigenvalue sync");
+    if (st) return fail(LBM_ECUDA, "the QR iteration did not converge for some point");
+    return LBM_OK;
+}
+
+int lbm_vn_stability_limit(int eq_kind, int64_t npairs, const double *nu, const double *theta, int nk,
+                           double u_hi, int iterations, double tol, double *umax, void *cuda_stream) {
+    if (eq_kind < 0 || eq_kind > 2 || npairs < 0 || (npairs > 0 && (!nu || !theta || !umax)) || nk < 1 ||
+        nk > 1024 || !(u_hi > 0) || u_hi >= 1.0 || iterations < 1 || iterations > 60 || !(tol >= 0))
+        return fail(LBM_EINVAL, "bad stability-limit arguments");
+    if (npairs == 0) return LBM_OK;
+    std::vector<double> tau(npairs), lo(npairs, 0.0), hi(npairs, u_hi), trial(npairs);
+    for (int64_t p = 0; p < npairs; ++p) {
+        if (!(nu[p] > 0)) return fail(LBM_EINVAL, "nu must be positive");
+        tau[p] = 0.5 + 3.0 * nu[p];
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    VnBufs b;
+    if (!b.alloc(0, sizeof(double) * npairs) || !b.alloc(1, sizeof(double) * npairs) ||
+        !b.alloc(2, sizeof(double) * npairs) || !b.alloc(3, sizeof(unsigned long long) * npairs) ||
+        !b.alloc(4, sizeof(int32_t)))
+        return fail(LBM_ENOMEM, "stability buffers");
+    CK(cudaMemcpyAsync(b.p[0], tau.data(), sizeof(double) * npairs, cudaMemcpyHostToDevice, s), "tau upload");
+    CK(cudaMemcpyAsync(b.p[1], theta, sizeof(double) * npairs, cudaMemcpyHostToDevice, s), "theta upload");
+    CK(cudaMemsetAsync(b.p[4], 0, sizeof(int32_t), s), "status clear");
+    std::vector<unsigned long long> bits(npairs);
+    // first probe u_hi itself (a pair stable there reports u_hi), then bisect [0, u_hi]
+    for (int it = 0; it <= iterations; ++it) {
+        for (int64_t p = 0; p < npairs; ++p) trial[p] = it == 0 ? u_hi : 0.5 * (lo[p] + hi[p]);
+        CK(cudaMemcpyAsync(b.p[2], trial.data(), sizeof(double) * npairs, cudaMemcpyHostToDevice, s), "trial upload");
+        CK(cudaMemsetAsync(b.p[3], 0, sizeof(unsigned long long) * npairs, s), "radius clear");
+        CK(vn_radius(eq_kind, npairs, (const double *)b.p[0], (const double *)b.p[1], (const double *)b.p[2], nk,
+                     (unsigned long long *)b.p[3], (int32_t *)b.p[4], s),
+           "spectral radius kernel");
+        CK(cudaMemcpyAsync(bits.data(), b.p[3], sizeof(unsigned long long) * npairs, cudaMemcpyDeviceToHost, s),
+           "radius copy");
+        CK(cudaStreamSynchronize(s), "radius sync");
+        for (int64_t p = 0; p < npairs; ++p) {
+            double r;
+            memcpy(&r, &bits[p], sizeof r);
+            const bool stable = r <= 1.0 + tol;
+            if (it == 0) {
+                if (stable) lo[p] = hi[p] = u_hi;
+            } else if (lo[p] < hi[p]) {
+                if (stable) lo[p] = trial[p];
+                else hi[p] = trial[p];
+            }
+        }
+    }
+    int32_t st = 0;
+    CK(cudaMemcpy(&st, b.p[4], sizeof(int32_t), cudaMemcpyDeviceToHost), "status copy");
+    if (st) return fail(LBM_ECUDA, "the QR iteration did not converge for some point");
+    for (int64_t p = 0; p < npairs; ++p) umax[p] = lo[p];
+    return LBM_OK;
+}
+
 int lbm_selftest_bounded_wait(void *cuda_stream, int64_t timeout_ns, int32_t *status_out) {
     if (!status_out || timeout_ns <= 0 || timeout_ns > 10000000000LL)
         return fail(LBM_EINVAL, "bad self-test arguments");

@@ -166,57 +166,124 @@ __device__ __forceinline__ void tma_plain_stores(const lbmh::StepArgs &a, const 
     }
 }
 
+// Shared-memory positions of one cell's populations (see the header comment): in the
+// even step direction i is read at x and written (as direction opp(i)) at x; in the odd
+// step it is read at x - c_ix and written at x + c_ix, wrapping inside a whole row.
+struct CellPos {
+    int row, x, xm, xp;
+};
+
+__device__ __forceinline__ CellPos cell_pos(const TmaGeom &g, int r, int xl, int len) {
+    CellPos p;
+    p.row = r * g.rowstride + g.halo;
+    p.x = xl;
+    p.xm = xl - 1;
+    p.xp = xl + 1;
+    if (g.nseg == 1) {
+        p.xm = xl == 0 ? len - 1 : p.xm;
+        p.xp = xl == len - 1 ? 0 : p.xp;
+    }
+    return p;
+}
+
+template <int D, int P, int CAPB>
+__device__ __forceinline__ void tma_load_cell(const typename Storage<P>::T *st, const CellPos &p,
+                                              int odd, typename Storage<P>::R (&f)[qof(D)]) {
+    using St = Storage<P>;
+    constexpr int bs = CAPB / (int)sizeof(typename St::T);  // compile-time offsets between buffers
+    const typename St::T *row = st + p.row;
+    if (!odd) {
+#pragma unroll
+        for (int i = 0; i < qof(D); ++i) f[i] = St::load(row[i * bs + p.x]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < qof(D); ++i) {
+            const int x = cxo(i) == 1 ? p.xm : (cxo(i) == -1 ? p.xp : p.x);
+            f[i] = St::load(row[i * bs + x]);
+        }
+    }
+}
+
+template <int D, int P, int CAPB>
+__device__ __forceinline__ void tma_store_cell(typename Storage<P>::T *st, const CellPos &p, int odd,
+                                               const typename Storage<P>::R (&f)[qof(D)]) {
+    using St = Storage<P>;
+    constexpr int Q = qof(D);
+    constexpr int bs = CAPB / (int)sizeof(typename St::T);
+    typename St::T *row = st + p.row;
+    if (!odd) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) row[(Q - 1 - i) * bs + p.x] = St::store(f[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int x = cxo(i) == 1 ? p.xp : (cxo(i) == -1 ? p.xm : p.x);
+            row[(Q - 1 - i) * bs + x] = St::store(f[i]);
+        }
+    }
+}
+
+// Collide every cell of a job in place in its stage.  With FP32 collisions each thread
+// takes two cells per iteration (c and c + nthr) and runs their loads and collisions as
+// independent chains, so the scheduler can overlap them; the second cell's stores are
+// skipped past the end.
 template <int D, int P, int EQ, bool BULK, int CAPB>
 __device__ __forceinline__ void tma_compute(const lbmh::StepArgs &a, const TmaGeom &g,
                                             const JobPos &j, typename Storage<P>::T *st,
                                             DiagAcc &acc, int tid, int nthr) {
     using St = Storage<P>;
-    using T = typename St::T;
     using R = typename St::R;
     constexpr int Q = qof(D);
-    constexpr int bs = CAPB / (int)sizeof(T);  // compile-time offsets between buffers
     const R rho0 = step_scalar<R>(a.rho0, a.rho0f), omega0 = step_scalar<R>(a.omega0, a.omega0f),
             six_nu = step_scalar<R>(a.six_nu, a.six_nuf);
-    const bool whole = g.nseg == 1;
     const int ncells = j.nrows * j.len;
     DiagLocal<R> loc;
-    // cell c of the job: row r = c / len, xl = c % len, advanced incrementally
-    int r = tid / j.len;
-    int xl = tid - r * j.len;
-    for (int c = tid; c < ncells; c += nthr) {
-        T *row = st + r * g.rowstride + g.halo;
-        int xm = xl - 1, xp = xl + 1;
-        if (whole) {
-            xm = xl == 0 ? j.len - 1 : xm;
-            xp = xl == j.len - 1 ? 0 : xp;
-        }
-        R f[Q];
-        if (!a.odd) {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) f[i] = St::load(row[i * bs + xl]);
-        } else {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int p = cxo(i) == 1 ? xm : (cxo(i) == -1 ? xp : xl);
-                f[i] = St::load(row[i * bs + p]);
+    if constexpr (P == P_F64) {
+        // FP64 collisions are bound by the FP64 pipe: one cell at a time (no spills)
+        int r = tid / j.len;
+        int xl = tid - r * j.len;
+        for (int c = tid; c < ncells; c += nthr) {
+            const CellPos p = cell_pos(g, r, xl, j.len);
+            R f[Q];
+            tma_load_cell<D, P, CAPB>(st, p, a.odd, f);
+            const CellMoments<R> m = collide<D, EQ, BULK, R>(f, rho0, omega0, six_nu);
+            tma_store_cell<D, P, CAPB>(st, p, a.odd, f);
+            if (a.diag) loc.add(m.rho, m.u, rho0);
+            xl += nthr;
+            while (xl >= j.len) {
+                xl -= j.len;
+                ++r;
             }
         }
-        const CellMoments<R> m = collide<D, EQ, BULK, R>(f, rho0, omega0, six_nu);
-        if (!a.odd) {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) row[(Q - 1 - i) * bs + xl] = St::store(f[i]);
-        } else {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int p = cxo(i) == 1 ? xp : (cxo(i) == -1 ? xm : xl);
-                row[(Q - 1 - i) * bs + p] = St::store(f[i]);
+    } else {
+        int rA = tid / j.len;
+        int xA = tid - rA * j.len;
+        for (int c = tid; c < ncells; c += 2 * nthr) {
+            int rB = rA, xB = xA + nthr;
+            while (xB >= j.len) {
+                xB -= j.len;
+                ++rB;
             }
-        }
-        if (a.diag) loc.add(m.rho, m.u, rho0);
-        xl += nthr;
-        while (xl >= j.len) {
-            xl -= j.len;
-            ++r;
+            const bool hasB = c + nthr < ncells;
+            const CellPos pA = cell_pos(g, rA, xA, j.len);
+            const CellPos pB = hasB ? cell_pos(g, rB, xB, j.len) : pA;
+            R fA[Q], fB[Q];
+            tma_load_cell<D, P, CAPB>(st, pA, a.odd, fA);
+            tma_load_cell<D, P, CAPB>(st, pB, a.odd, fB);
+            const CellMoments<R> mA = collide<D, EQ, BULK, R>(fA, rho0, omega0, six_nu);
+            const CellMoments<R> mB = collide<D, EQ, BULK, R>(fB, rho0, omega0, six_nu);
+            tma_store_cell<D, P, CAPB>(st, pA, a.odd, fA);
+            if (hasB) tma_store_cell<D, P, CAPB>(st, pB, a.odd, fB);
+            if (a.diag) {
+                loc.add(mA.rho, mA.u, rho0);
+                if (hasB) loc.add(mB.rho, mB.u, rho0);
+            }
+            rA = rB;
+            xA = xB + nthr;
+            while (xA >= j.len) {
+                xA -= j.len;
+                ++rA;
+            }
         }
     }
     if (a.diag) loc.flush(acc, a.rho0);

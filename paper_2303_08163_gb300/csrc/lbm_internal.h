@@ -106,4 +106,10 @@ cudaError_t batch_populations(const double *arena, const int64_t *cell_start,
                               const int32_t *dims, int64_t count, int D, double rho0, int odd,
                               void *f, int dtype, int64_t total_cells, cudaStream_t s);
 
+// k_vn.cu
+cudaError_t vn_eigs(int eq, int bulk, int64_t count, const double *params, double *out, int32_t *status,
+                    cudaStream_t s);
+cudaError_t vn_radius(int eq, int64_t npairs, const double *tau, const double *theta, const double *u_try, int nk,
+                      unsigned long long *radius_bits, int32_t *status, cudaStream_t s);
+
 }  // namespace lbmh

@@ -133,9 +133,50 @@ def random_solenoidal(dims, u_rms=0.05, k_peak=8.0, seed=2303):
     # arrays are indexed [x, y, z]; the library wants x fastest (z, y, x order)
     u = [np.fft.irfftn(cv, s=(nx, ny, nz)).transpose(2, 1, 0).reshape(-1) for cv in comps]
     u = np.stack(u)
-    scale = u_rms / np.sqrt(np.mean(u * u) )
+    scale = u_rms / np.sqrt(np.mean(u * u))
     u *= scale
     rho = np.ones(nx * ny * nz)
+    return rho, u
+
+
+def random_solenoidal_torch(dims, u_rms=0.05, k_peak=8.0, seed=2303, device="cuda"):
+    """The field of random_solenoidal, generated with torch (on a GPU for the full-size
+    1024 x 512 x 512 box) from a seeded torch generator.  Returns float32 tensors rho
+    (ncell,) and u (3, ncell) on `device`, x fastest."""
+    import torch
+    nx, ny, nz = dims
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    f64 = torch.float64
+    kx = torch.fft.fftfreq(nx, d=1.0 / nx, device=device, dtype=f64) * (ny / nx)
+    ky = torch.fft.fftfreq(ny, d=1.0 / ny, device=device, dtype=f64)
+    kz = torch.fft.rfftfreq(nz, d=1.0 / nz, device=device, dtype=f64)
+    KX, KY, KZ = torch.meshgrid(kx, ky, kz, indexing="ij")
+    k2 = KX ** 2 + KY ** 2 + KZ ** 2
+    safe = torch.where(k2 > 0, k2, torch.ones_like(k2))
+    amp = torch.sqrt(k2 * k2 * torch.exp(-2.0 * k2 / (k_peak * k_peak)) / (4 * math.pi * safe))
+    amp[k2 == 0] = 0.0
+    comps = []
+    for _ in range(3):
+        re = torch.randn(KX.shape, generator=gen, device=device, dtype=f64)
+        im = torch.randn(KX.shape, generator=gen, device=device, dtype=f64)
+        comps.append(amp * torch.complex(re, im))
+    del re, im, amp
+    kdotv = (KX * comps[0] + KY * comps[1] + KZ * comps[2]) / safe
+    comps = [comps[0] - KX * kdotv, comps[1] - KY * kdotv, comps[2] - KZ * kdotv]
+    del kdotv, KX, KY, KZ, k2, safe
+    u = torch.empty((3, nx * ny * nz), device=device, dtype=torch.float32)
+    sq = 0.0
+    for a in range(3):
+        ua = torch.fft.irfftn(comps[a], s=(nx, ny, nz))  # indexed [x, y, z]
+        comps[a] = None
+        ua = ua.permute(2, 1, 0).contiguous().reshape(-1)  # x fastest
+        sq += float(torch.sum(ua * ua))
+        u[a] = ua.float()
+        del ua
+    scale = u_rms / math.sqrt(sq / (3 * nx * ny * nz))
+    u *= scale
+    rho = torch.ones(nx * ny * nz, device=device, dtype=torch.float32)
     return rho, u
 
 

@@ -73,6 +73,8 @@ SIGNATURES = {
     "lbm_version": (_i, []),
     "lbm_selftest_bounded_wait": (_i, [_vp, _i64, _pi32]),
     "lbm_diagnostics_noalloc": (_i, [_i, _p64, _vp, _i64, _vp, _vp]),
+    "lbm_vn_eigenvalues": (_i, [_i, _i, _i64, _pdbl, _pdbl, _vp]),
+    "lbm_vn_stability_limit": (_i, [_i, _i64, _pdbl, _pdbl, _i, _d, _i, _d, _pdbl, _vp]),
 }
 
 _lib = None
@@ -360,6 +362,28 @@ def diagnostics_noalloc(lattice, dims, f, out, blocks=256, stream=None):
     d = (ctypes.c_int64 * 3)(*(list(dims) + [1, 1, 1])[:3])
     _check(load().lbm_diagnostics_noalloc(int(lattice), d, ctypes.c_void_p(f.data_ptr()), int(blocks),
                                           ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+
+
+def vn_eigenvalues(eq_kind, bulk_corr, params, stream=None):
+    """Eigenvalues (count, 9) complex of M = E (delta + J) for params (count, 6) =
+    (tau, rho, u_x, u_y, k_x, k_y), sorted by decreasing modulus (lbm_vn_eigenvalues)."""
+    p = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 6)
+    out = np.zeros((len(p), 9, 2))
+    _check(load().lbm_vn_eigenvalues(int(eq_kind), int(bulk_corr), len(p), p.ctypes.data_as(_pdbl),
+                                     out.ctypes.data_as(_pdbl), _stream_handle(stream)))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def vn_stability_limit(eq_kind, nu, theta, nk=33, u_hi=0.999, iterations=20, tol=1e-10, stream=None):
+    """Largest linearly stable |u| per (nu, theta) pair (lbm_vn_stability_limit)."""
+    nu = np.ascontiguousarray(nu, dtype=np.float64).reshape(-1)
+    theta = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1)
+    out = np.zeros(len(nu))
+    _check(load().lbm_vn_stability_limit(int(eq_kind), len(nu), nu.ctypes.data_as(_pdbl),
+                                         theta.ctypes.data_as(_pdbl), int(nk), float(u_hi),
+                                         int(iterations), float(tol), out.ctypes.data_as(_pdbl),
+                                         _stream_handle(stream)))
+    return out
 
 
 def selftest_bounded_wait(timeout_ns=1_000_000, stream=None):
