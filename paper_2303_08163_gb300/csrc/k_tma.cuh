@@ -223,10 +223,7 @@ __device__ __forceinline__ void tma_store_cell(typename Storage<P>::T *st, const
     }
 }
 
-// Collide every cell of a job in place in its stage.  With FP32 collisions each thread
-// takes two cells per iteration (c and c + nthr) and runs their loads and collisions as
-// independent chains, so the scheduler can overlap them; the second cell's stores are
-// skipped past the end.
+// Collide every cell of a job in place in its stage, one cell per thread per iteration.
 template <int D, int P, int EQ, bool BULK, int CAPB>
 __device__ __forceinline__ void tma_compute(const lbmh::StepArgs &a, const TmaGeom &g,
                                             const JobPos &j, typename Storage<P>::T *st,
@@ -238,52 +235,19 @@ __device__ __forceinline__ void tma_compute(const lbmh::StepArgs &a, const TmaGe
             six_nu = step_scalar<R>(a.six_nu, a.six_nuf);
     const int ncells = j.nrows * j.len;
     DiagLocal<R> loc;
-    if constexpr (P == P_F64) {
-        // FP64 collisions are bound by the FP64 pipe: one cell at a time (no spills)
-        int r = tid / j.len;
-        int xl = tid - r * j.len;
-        for (int c = tid; c < ncells; c += nthr) {
-            const CellPos p = cell_pos(g, r, xl, j.len);
-            R f[Q];
-            tma_load_cell<D, P, CAPB>(st, p, a.odd, f);
-            const CellMoments<R> m = collide<D, EQ, BULK, R>(f, rho0, omega0, six_nu);
-            tma_store_cell<D, P, CAPB>(st, p, a.odd, f);
-            if (a.diag) loc.add(m.rho, m.u, rho0);
-            xl += nthr;
-            while (xl >= j.len) {
-                xl -= j.len;
-                ++r;
-            }
-        }
-    } else {
-        int rA = tid / j.len;
-        int xA = tid - rA * j.len;
-        for (int c = tid; c < ncells; c += 2 * nthr) {
-            int rB = rA, xB = xA + nthr;
-            while (xB >= j.len) {
-                xB -= j.len;
-                ++rB;
-            }
-            const bool hasB = c + nthr < ncells;
-            const CellPos pA = cell_pos(g, rA, xA, j.len);
-            const CellPos pB = hasB ? cell_pos(g, rB, xB, j.len) : pA;
-            R fA[Q], fB[Q];
-            tma_load_cell<D, P, CAPB>(st, pA, a.odd, fA);
-            tma_load_cell<D, P, CAPB>(st, pB, a.odd, fB);
-            const CellMoments<R> mA = collide<D, EQ, BULK, R>(fA, rho0, omega0, six_nu);
-            const CellMoments<R> mB = collide<D, EQ, BULK, R>(fB, rho0, omega0, six_nu);
-            tma_store_cell<D, P, CAPB>(st, pA, a.odd, fA);
-            if (hasB) tma_store_cell<D, P, CAPB>(st, pB, a.odd, fB);
-            if (a.diag) {
-                loc.add(mA.rho, mA.u, rho0);
-                if (hasB) loc.add(mB.rho, mB.u, rho0);
-            }
-            rA = rB;
-            xA = xB + nthr;
-            while (xA >= j.len) {
-                xA -= j.len;
-                ++rA;
-            }
+    int r = tid / j.len;
+    int xl = tid - r * j.len;
+    for (int c = tid; c < ncells; c += nthr) {
+        const CellPos p = cell_pos(g, r, xl, j.len);
+        R f[Q];
+        tma_load_cell<D, P, CAPB>(st, p, a.odd, f);
+        const CellMoments<R> m = collide<D, EQ, BULK, R>(f, rho0, omega0, six_nu);
+        tma_store_cell<D, P, CAPB>(st, p, a.odd, f);
+        if (a.diag) loc.add(m.rho, m.u, rho0);
+        xl += nthr;
+        while (xl >= j.len) {
+            xl -= j.len;
+            ++r;
         }
     }
     if (a.diag) loc.flush(acc, a.rho0);
@@ -319,6 +283,7 @@ __global__ void __launch_bounds__(kTmaMaxThreads + 32) k_step_tma(const lbmh::St
             const int64_t job = blockIdx.x + k * G;
             if (job >= g.njobs) break;
             const int s = (int)(k % S);
+            const JobPos jp = decode_job(a, g, job);
             if (k >= S) {
                 // stage s still holds job k - S: wait for its collision, store it back
                 const int64_t q = k - S;
@@ -328,18 +293,24 @@ __global__ void __launch_bounds__(kTmaMaxThreads + 32) k_step_tma(const lbmh::St
                     break;
                 }
                 const JobPos jq = decode_job(a, g, blockIdx.x + q * G);
-                if (a.odd && g.nseg > 1) tma_plain_stores<D, T>(a, g, jq, sm + s * stage_elems, lane, 32);
+                if (a.odd && g.nseg > 1) {
+                    tma_plain_stores<D, T>(a, g, jq, sm + s * stage_elems, lane, 32);
+                    __syncwarp();  // every lane's plain stores read the stage before any refill
+                }
+                if (lane == 0) mbar_arrive_expect_tx(&full[s], tma_job_bytes<D, T>(a, g, jp));
                 if (lane < Q) {
+                    // each lane stores its direction's buffer, waits until that store has
+                    // read shared memory, and refills the same buffer; lanes do not wait
+                    // for one another (the stage's phase completes once all bytes land)
                     tma_issue_stores<D, T>(a, g, jq, lane, sm + s * stage_elems);
                     bulk_commit();
-                    bulk_wait_read<0>();  // this lane's stores have read its buffer
+                    bulk_wait_read<0>();
+                    tma_issue_loads<D, T>(a, g, jp, lane, sm + s * stage_elems, &full[s]);
                 }
-                __syncwarp();  // plain stores of all lanes read the stage before the refill
+            } else {
+                if (lane == 0) mbar_arrive_expect_tx(&full[s], tma_job_bytes<D, T>(a, g, jp));
+                if (lane < Q) tma_issue_loads<D, T>(a, g, jp, lane, sm + s * stage_elems, &full[s]);
             }
-            const JobPos jp = decode_job(a, g, job);
-            if (lane == 0) mbar_arrive_expect_tx(&full[s], tma_job_bytes<D, T>(a, g, jp));
-            __syncwarp();
-            if (lane < Q) tma_issue_loads<D, T>(a, g, jp, lane, sm + s * stage_elems, &full[s]);
         }
         const int64_t issued = k;
         if (!failed) {
