@@ -5,8 +5,15 @@ Re = 1600 with nu = u0 (N / 2 pi) / Re), entropic equilibrium, populations store
 binary16 f - w rho0 with FP32 collision, fused diagnostics every 10 steps.  One bench
 step is one lattice time step of the whole grid.  Prints one JSON line.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload tgv3d|shear2d|tgv2d|batch]
+  python bench.py [--gpus N] [--steps K] [--warmup W]
+                  [--workload tgv3d|shear2d|tgv2d|batch|turb3d]
                   [--precision f16s|f32|f64] [--impl reference]
+  python bench.py --accuracy [--workload tgv3d|shear2d] [--long-steps S]
+
+--accuracy prints the long accuracy checks instead of a bench line: on the Taylor-Green
+vortex the FP32 and binary16 velocity error against FP64 storage after four convective
+times and the binary16-vs-FP32 energy and dissipation curves over 20000 steps; on the
+shear layer the step at which each equilibrium first goes non-finite within 10000 steps.
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same workload
 (rank 0 only).  Under torchrun (N > 1) every rank runs an independent replica of the
@@ -31,6 +38,27 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "GLUPS and % of HBM roofline; FP16-store vs FP32/FP64 at stated L2 velocity error"
+
+
+def fp64_flops_per_cell(eq, bulk):
+    """Algorithmic FP64 flops of one D2Q9 collision as the kernels write it (an FMA is two
+    flops, a division or a square root one).  Common part 29: moments 18 (15 adds, one
+    division, two multiplies), drho 1, and the rate terms 10 (1 - 2beta and, per weight
+    class, 2beta w, 2beta w rho, 2beta w drho).  Entropic: per axis u^2, S and 1 + S
+    (2 x 5), one shared reciprocal of (1 + S_x)(1 + S_y) and its two cofactors (4), per
+    axis S - 1, d(+1) and d(-1) (2 x 8), t = 1 + d 3, per direction h and the relaxation
+    9 x 6.  Quadratic: u^2 3, -3/2 u^2 1,
+    the diagonal sums 2, per direction 9 x 8.  Product form: per-axis factors 2 x 7,
+    t = 1 + d 3, 9 x 6.  The bulk correction adds the rate formula (6 entropic, 5
+    otherwise)."""
+    base = 18 + 1 + 10
+    if eq == 0:
+        return base + 30 + 3 + 54 + (6 if bulk else 0)
+    if eq == 1:
+        return base + 3 + 1 + 2 + 72 + (5 if bulk else 0)
+    return base + 14 + 3 + 54 + (5 if bulk else 0)
+
+
 PREC = {"f64": 0, "f32": 1, "f16s": 2}
 ESIZE = {0: 8, 1: 4, 2: 2}
 PREC_NAME = {0: "F64", 1: "F32", 2: "F16S"}
@@ -50,6 +78,11 @@ def parse():
     p.add_argument("--diag-every", type=int, default=10)
     p.add_argument("--no-extras", action="store_true", help="skip the comparison runs")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--accuracy", action="store_true",
+                   help="only run the long accuracy checks of the workload (Taylor-Green: FP32 and "
+                        "binary16 against FP64; shear layer: divergence step) and print them")
+    p.add_argument("--long-steps", type=int, default=None,
+                   help="steps of the long accuracy runs (Taylor-Green 20000, shear layer 10000)")
     p.add_argument("--no-tune", action="store_true",
                    help="keep the default (or cached) launch shape instead of autotuning")
     return p.parse_args()
@@ -335,6 +368,16 @@ def run_native(args):
     D, dims, prec = w["D"], w["dims"], w["prec"]
     Q = 3 ** D
     ncell = int(np.prod(dims))
+    if args.accuracy:
+        rho, u = fields_device(w, torch, dev)
+        if rank == 0:
+            if D == 3 and "Taylor" in w["name"]:
+                args.long_steps = args.long_steps or 20000
+                res = accuracy_gates(torch, lbm, dev, w, args, rho, u)
+            else:
+                res = shear_divergence(torch, lbm, w, args, rho, u, steps=args.long_steps or 10000)
+            print(json.dumps({"accuracy": res, "workload": w["name"]}), flush=True)
+        return
     lat = lbm.Lattice(lbm.D3Q27 if D == 3 else lbm.D2Q9, dims, w["tau"], w["eq"], args.bulk, prec)
     rho, u = fields_device(w, torch, dev)
     lat.init_fields(rho, u, dtype=np.float32)
@@ -410,6 +453,8 @@ def run_native(args):
         extras["precision_compare"] = compare_precisions(torch, lbm, dev, w, args, rho, u)
         if "turbulence" in w["name"]:
             extras["energy_decay"] = energy_decay_compare(torch, lbm, w, args, rho, u)
+        elif "shear" in w["name"]:
+            extras["divergence"] = shear_divergence(torch, lbm, w, args, rho, u)
         elif w["D"] == 3:
             extras["l2_velocity_error"] = velocity_error(torch, lbm, dev)
     cpu = None
@@ -467,6 +512,102 @@ def energy_decay_compare(torch, lbm, w, args, rho, u, steps=5000, every=100):
             "E_last_over_E0": curves[1][common[-1]] / curves[1][common[0]] if common else None,
             "nonfinite_from_step": {"F16S": diverged[2], "F32": diverged[1]},
             "note": "constant-tau BGK at tau - 1/2 = 1e-4 without a nonlinear limiter"}
+
+
+def energy_curve(torch, lbm, D, dims, tau, eq, bulk, prec, rho, u, steps, every):
+    """Run one lattice for `steps` steps with fused diagnostics every `every` steps.
+    Returns {step: kinetic energy} over the finite records, the first step with a
+    non-finite cell (None if none) and the device seconds taken."""
+    lat = lbm.Lattice(lbm.D3Q27 if D == 3 else lbm.D2Q9, dims, tau, eq, bulk, prec)
+    lat.init_fields(rho, u, dtype=np.float32)
+    lat.set_option(lbm.OPT_DIAG_EVERY, every)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    try:
+        lat.step(steps + 1)
+    except lbm.LBMError as e:
+        if e.status != lbm.ENONFINITE:
+            raise
+    e1.record()
+    e1.synchronize()
+    hist = lat.diag_history()
+    lat.close()
+    torch.cuda.empty_cache()
+    bad = [h["step"] for h in hist if h["nonfinite"] > 0 or not np.isfinite(h["kinetic"])]
+    curve = {h["step"]: h["kinetic"] for h in hist if h["nonfinite"] == 0 and np.isfinite(h["kinetic"])}
+    return curve, (bad[0] if bad else None), e0.elapsed_time(e1) * 1e-3
+
+
+def shear_divergence(torch, lbm, w, args, rho, u, steps=10000, every=100):
+    """Double shear layer at tau - 1/2 = 3e-5 (a nearly inviscid flow the paper's linear
+    analysis does not cover): the step at which each equilibrium first produced a
+    non-finite cell within `steps` steps (None: it stayed finite), reported, not asserted."""
+    out = {"steps": steps, "every": every}
+    for name, eq in (("entropic", 0), ("poly2", 1)):
+        curve, bad, sec = energy_curve(torch, lbm, w["D"], w["dims"], w["tau"], eq, args.bulk, w["prec"],
+                                       rho, u, steps, every)
+        t = sorted(curve)
+        out[name] = {"nonfinite_from_step": bad, "last_finite_record": t[-1] if t else None,
+                     "E_last_over_E0": curve[t[-1]] / curve[t[0]] if t else None, "seconds": sec}
+    return out
+
+
+def accuracy_gates(torch, lbm, dev, w, args, rho, u):
+    """Accuracy of the reduced-precision storage on the full-size Taylor-Green vortex at
+    Re = 1600: (i) relative L2 velocity error of FP32 and binary16 storage against FP64
+    storage after four convective times t_c = N / (2 pi u0), while the flow is still
+    laminar and pointwise differences are meaningful; (ii) over `long_steps` steps, the
+    kinetic-energy curve E(t) and the dissipation -dE/dt of binary16 against FP32, with
+    the bulk correction off and on (after transition pointwise fields decorrelate, so the
+    volume averages are compared)."""
+    D, dims, ncell = w["D"], w["dims"], int(np.prod(w["dims"]))
+    n = dims[0]
+    steps_i = int(round(4 * n / (2 * math.pi * w["u0"])))
+    out = {"pointwise": {"steps": steps_i}, "curves": {}}
+    vel = {}
+    for prec in (0, 1, 2):
+        lat = lbm.Lattice(lbm.D3Q27, dims, w["tau"], w["eq"], 0, prec)
+        lat.init_fields(rho, u, dtype=np.float32)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        lat.step(steps_i)
+        e1.record()
+        r = torch.empty(ncell, device=dev, dtype=torch.float64)
+        v = torch.empty(3, ncell, device=dev, dtype=torch.float64)
+        lat.moments(dtype=np.float64, out=(r, v))
+        torch.cuda.synchronize()
+        out["pointwise"][PREC_NAME[prec] + "_seconds"] = e0.elapsed_time(e1) * 1e-3
+        lat.close()
+        del r
+        vel[prec] = v
+        torch.cuda.empty_cache()
+    ref = torch.linalg.norm(vel[0])
+    for prec in (1, 2):
+        out["pointwise"][PREC_NAME[prec] + "_rel_l2_vs_F64"] = float(torch.linalg.norm(vel[prec] - vel[0]) / ref)
+    del vel
+    torch.cuda.empty_cache()
+    every = 100
+    for bulk in (0, 1):
+        curves, bad = {}, {}
+        for prec in (1, 2):
+            curves[prec], bad[prec], _ = energy_curve(torch, lbm, D, dims, w["tau"], w["eq"], bulk, prec,
+                                                      rho, u, args.long_steps, every)
+        common = sorted(set(curves[1]) & set(curves[2]))
+        e32 = np.array([curves[1][t] for t in common])
+        e16 = np.array([curves[2][t] for t in common])
+        res = {"nonfinite_from_step": {"F32": bad[1], "F16S": bad[2]},
+               "compared_until": common[-1] if common else None}
+        if len(common) > 2:
+            tt = np.array(common, dtype=float)
+            d32, d16 = -np.gradient(e32, tt), -np.gradient(e16, tt)
+            res.update({"E_max_rel_diff": float(np.max(np.abs(e16 - e32) / e32)),
+                        "dissipation_max_diff_over_peak": float(np.max(np.abs(d16 - d32)) / np.max(np.abs(d32))),
+                        "dissipation_peak_step": int(tt[np.argmax(d32)]),
+                        "E_last_over_E0": float(e32[-1] / e32[0])})
+        out["curves"]["bulk" if bulk else "no_bulk"] = res
+    out["case"] = (f"{w['name']}, tau={w['tau']:.6f}; (i) {steps_i} steps, (ii) {args.long_steps} steps, "
+                   f"diagnostics every {every}")
+    return out
 
 
 def compare_precisions(torch, lbm, dev, w, args, rho, u):
@@ -527,19 +668,26 @@ def run_batch(args, w, torch, lbm, dev, rank, ws):
         e1.synchronize()
     ms = e0.elapsed_time(e1)
     glups = total * args.steps / (ms * 1e-3) / 1e9
-    algo = 2 * 9 * 8 * total * args.steps
-    peak = measured_peaks().get("hbm_gbs") or 6800.0
+    # FP64 collisions: the roofline is the FP64 pipe.  Peak = 152 SMs x 2 FP64 FMA per
+    # cycle x 2 flops x the median SM clock under load
+    fpc = fp64_flops_per_cell(w["eq"], args.bulk)
+    clocks = clk.summary()
+    sm_ghz = (clocks.get("sm_mhz") or 2070.0) / 1e3
+    fp64_peak = 152 * 2 * 2 * sm_ghz  # GFLOP/s
+    achieved = fpc * glups  # GFLOP/s
+    hbm = 2 * 9 * 8 * glups
     g, desc = oracle_sample(w, args.cpu_seconds)
     line = {"metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w["name"], "total_cells": total, "probe_every": 10,
                        "launch": b.launch_info()},
-            "roofline": {"bound": "hbm", "achieved": algo / (ms * 1e-3) / 1e9, "peak": peak,
-                         "unit": "GB/s", "frac": algo / (ms * 1e-3) / 1e9 / peak, "traffic": None,
-                         "note": "FP64 collision: bound by the FP64 pipe, not by HBM"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "GFLOP/s (FP64)",
+                         "frac": achieved / fp64_peak, "traffic": None,
+                         "flops_per_cell_update": fpc,
+                         "hbm_GB_s": hbm, "hbm_frac": hbm / (measured_peaks().get("hbm_gbs") or 6800.0)},
             "cpu_baseline": {"value": g, "unit": "GLUPS", "cores": 1, "kind": "oracle", "sample": desc},
-            "gpu_launches": 1, "clocks": clk.summary()}
+            "gpu_launches": 1, "clocks": clocks}
     print(json.dumps(line), flush=True)
 
 

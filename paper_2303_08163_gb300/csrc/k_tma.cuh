@@ -253,6 +253,128 @@ __device__ __forceinline__ void tma_compute(const lbmh::StepArgs &a, const TmaGe
     if (a.diag) loc.flush(acc, a.rho0);
 }
 
+// binary16 storage: the same collision, two neighbouring cells per thread per iteration,
+// so that every buffer position pair the two cells own at an even offset moves as one
+// 32-bit shared-memory access and one paired conversion.  Even step: cells (x, x + 1),
+// x even, own the pair at x in every buffer.  Odd step, whole rows: cells (x, x + 1), x
+// odd (the last pair is (len - 1, 0)), own the pairs at x - 1 and x + 1 in the buffers
+// with c_x != 0; the c_x = 0 buffers go one half at a time.  Odd step, segments (no wrap
+// inside the job): cells (x, x + 1), x even, own the pair at x in the c_x = 0 buffers and
+// go one half at a time elsewhere.  The conversions round exactly as the one-cell path
+// does, so the stored state is the same bit for bit.
+__device__ __forceinline__ float2 ld_pair(const __half *b, int p) {
+    return __half22float2(*reinterpret_cast<const __half2 *>(b + p));
+}
+__device__ __forceinline__ void st_pair(__half *b, int p, float lo, float hi) {
+    *reinterpret_cast<__half2 *>(b + p) = __floats2half2_rn(lo, hi);
+}
+
+// MODE 0: even step; 1: odd step, whole rows; 2: odd step, segments; -1: chosen at run
+// time from the step parity and the job layout (one loop body for all three).
+template <int D, int EQ, bool BULK, int CAPB, int MODE>
+__device__ __forceinline__ void tma_compute_pairs(const lbmh::StepArgs &a, const TmaGeom &g,
+                                                  const JobPos &j, __half *st, DiagAcc &acc,
+                                                  int tid, int nthr) {
+    constexpr int Q = qof(D);
+    constexpr int bs = CAPB / 2;  // halves between direction buffers
+    const int mode = MODE >= 0 ? MODE : (!a.odd ? 0 : (g.nseg == 1 ? 1 : 2));
+    const float rho0 = a.rho0f, omega0 = a.omega0f, six_nu = a.six_nuf;
+    const int hl = j.len >> 1;  // len is a multiple of 8 cells (16-byte rows)
+    const int npairs = j.nrows * hl;
+    DiagLocal<float> loc;
+    int r = tid / hl;
+    int xh = tid - r * hl;
+    for (int c = tid; c < npairs; c += nthr) {
+        __half *row = st + r * g.rowstride + g.halo;
+        // cells xa and xb = xa + 1 (the odd pairing of whole rows wraps its last pair to
+        // cell 0); pm = xa - 1 and pp = xb + 1 are the outer neighbours, inside the row for
+        // whole rows (xa >= 1 in the odd pairing) and in the halos for segments
+        const int xa = 2 * xh + (mode == 1 ? 1 : 0);
+        const int xb = (mode == 1 && xa + 1 == j.len) ? 0 : xa + 1;
+        const int pm = xa - 1;
+        const int pp = xb + 1;
+        float fa[Q], fb[Q];
+        if (mode == 0) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const float2 v = ld_pair(row + i * bs, xa);
+                fa[i] = v.x;
+                fb[i] = v.y;
+            }
+        } else if (mode == 1) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const __half *b = row + i * bs;
+                if (cxo(i) == 0) {
+                    fa[i] = __half2float(b[xa]);
+                    fb[i] = __half2float(b[xb]);
+                } else {
+                    const float2 v = ld_pair(b, cxo(i) == 1 ? pm : xb);
+                    fa[i] = v.x;
+                    fb[i] = v.y;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const __half *b = row + i * bs;
+                if (cxo(i) == 0) {
+                    const float2 v = ld_pair(b, xa);
+                    fa[i] = v.x;
+                    fb[i] = v.y;
+                } else if (cxo(i) == 1) {
+                    fa[i] = __half2float(b[pm]);
+                    fb[i] = __half2float(b[xa]);
+                } else {
+                    fa[i] = __half2float(b[xb]);
+                    fb[i] = __half2float(b[pp]);
+                }
+            }
+        }
+        const CellMoments<float> ma = collide<D, EQ, BULK, float>(fa, rho0, omega0, six_nu);
+        const CellMoments<float> mb = collide<D, EQ, BULK, float>(fb, rho0, omega0, six_nu);
+        if (mode == 0) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) st_pair(row + (Q - 1 - i) * bs, xa, fa[i], fb[i]);
+        } else if (mode == 1) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                __half *b = row + (Q - 1 - i) * bs;
+                if (cxo(i) == 0) {
+                    b[xa] = __float2half_rn(fa[i]);
+                    b[xb] = __float2half_rn(fb[i]);
+                } else {
+                    st_pair(b, cxo(i) == 1 ? xb : pm, fa[i], fb[i]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                __half *b = row + (Q - 1 - i) * bs;
+                if (cxo(i) == 0) {
+                    st_pair(b, xa, fa[i], fb[i]);
+                } else if (cxo(i) == 1) {
+                    b[xb] = __float2half_rn(fa[i]);
+                    b[pp] = __float2half_rn(fb[i]);
+                } else {
+                    b[pm] = __float2half_rn(fa[i]);
+                    b[xa] = __float2half_rn(fb[i]);
+                }
+            }
+        }
+        if (a.diag) {
+            loc.add(ma.rho, ma.u, rho0);
+            loc.add(mb.rho, mb.u, rho0);
+        }
+        xh += nthr;
+        while (xh >= hl) {
+            xh -= hl;
+            ++r;
+        }
+    }
+    if (a.diag) loc.flush(acc, a.rho0);
+}
+
 template <int D, int P, int EQ, bool BULK, int CAPB>
 __global__ void __launch_bounds__(kTmaMaxThreads + 32) k_step_tma(const lbmh::StepArgs a, const TmaGeom g) {
     using T = typename Storage<P>::T;
@@ -348,7 +470,19 @@ __global__ void __launch_bounds__(kTmaMaxThreads + 32) k_step_tma(const lbmh::St
             }
             T *st = sm + s * stage_elems;
             const JobPos jp = decode_job(a, g, job);
-            tma_compute<D, P, EQ, BULK, CAPB>(a, g, jp, st, acc, threadIdx.x, ncons);
+            if constexpr (P == P_F16S && D == 3) {
+                // the D3Q27 pair body is long: one copy serves the three pairings (three
+                // specialised copies measured slower)
+                tma_compute_pairs<D, EQ, BULK, CAPB, -1>(a, g, jp, st, acc, threadIdx.x, ncons);
+            } else if constexpr (P == P_F16S) {
+                if (!a.odd)
+                    tma_compute_pairs<D, EQ, BULK, CAPB, 0>(a, g, jp, st, acc, threadIdx.x, ncons);
+                else if (g.nseg == 1)
+                    tma_compute_pairs<D, EQ, BULK, CAPB, 1>(a, g, jp, st, acc, threadIdx.x, ncons);
+                else
+                    tma_compute_pairs<D, EQ, BULK, CAPB, 2>(a, g, jp, st, acc, threadIdx.x, ncons);
+            } else
+                tma_compute<D, P, EQ, BULK, CAPB>(a, g, jp, st, acc, threadIdx.x, ncons);
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive_cta(&empty[s]);

@@ -122,6 +122,47 @@ __host__ __device__ __forceinline__ void axis_factors(R u, R &dm, R &d0, R &dp, 
     }
 }
 
+// The per-axis factors of all D axes.  In FP64 the entropic form's D divisions
+// 3u_a^2 / (1 + S_a) share one reciprocal of the product of the (1 + S_a), each axis
+// multiplying it by the other axes' factors (a few ulp, one IEEE division instead of D;
+// FP64 divisions are long instruction sequences on the FP64 pipe).
+template <int D, int EQ, typename R>
+__host__ __device__ __forceinline__ void all_axis_factors(const R (&u)[3], R (&dm)[3], R (&d0)[3],
+                                                          R (&dp)[3], R (&key)[3]) {
+    if constexpr (EQ == EQ_ENT && sizeof(R) == 8) {
+        R u2[3], S[3], op[3];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            u2[a] = u[a] * u[a];
+            S[a] = sqrt_r(fma_r(R(3), u2[a], R(1)));
+            op[a] = R(1) + S[a];
+        }
+        R inv[3];
+        if constexpr (D == 2) {
+            const R r = R(1) / (op[0] * op[1]);
+            inv[0] = r * op[1];
+            inv[1] = r * op[0];
+        } else {
+            const R yz = op[1] * op[2];
+            const R r = R(1) / (op[0] * yz);
+            inv[0] = r * yz;
+            inv[1] = r * (op[0] * op[2]);
+            inv[2] = r * (op[0] * op[1]);
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const R sm1 = R(3) * u2[a] * inv[a];  // S - 1 without cancellation
+            d0[a] = -sm1;
+            dp[a] = fma_r(R(2), sm1, R(3) * u[a]);
+            dm[a] = fma_r(R(2), sm1, R(-3) * u[a]);
+            key[a] = S[a];
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < D; ++a) axis_factors<EQ>(u[a], dm[a], d0[a], dp[a], key[a]);
+    }
+}
+
 // Local collision frequency 2 beta from the largest per-axis key.
 template <int EQ, bool BULK, typename R>
 __host__ __device__ __forceinline__ R collision_rate(R key_max, R omega0, R six_nu) {
@@ -172,8 +213,7 @@ __host__ __device__ __forceinline__ R equilibrium_h(const R (&u)[3], R (&h)[qof(
         return k;
     } else {
         R dm[3], d0[3], dp[3], key[3];
-#pragma unroll
-        for (int a = 0; a < D; ++a) axis_factors<EQ>(u[a], dm[a], d0[a], dp[a], key[a]);
+        all_axis_factors<D, EQ>(u, dm, d0, dp, key);
         R kmax = fmax(key[0], key[1]);
         if constexpr (D == 3) kmax = fmax(kmax, key[2]);
         // d and t = 1 + d per axis, indexed by c + 1
@@ -253,7 +293,11 @@ __host__ __device__ __forceinline__ CellMoments<R> collide(R (&f)[qof(D)], R rho
         const R om = collision_rate<EQ, BULK, R>(k, omega0, six_nu);
         const R keep = R(1) - om;
         const R mh = R(-1.5) * uu;
+        // per weight class: 2beta w rho and 2beta w drho, so that each direction costs
+        // two FMAs after its h: f* = (2beta w rho) h + ((1 - 2beta) f + 2beta w drho)
         const R omw[4] = {om * R(kW0), om * R(kW1), om * R(kW2), om * R(kW3)};
+        const R wr[4] = {omw[0] * m.rho, omw[1] * m.rho, omw[2] * m.rho, omw[3] * m.rho};
+        const R wd[4] = {omw[0] * drho, omw[1] * drho, omw[2] * drho, omw[3] * drho};
         const R upm = m.u[0] + m.u[1], umm = m.u[0] - m.u[1];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -267,17 +311,20 @@ __host__ __device__ __forceinline__ CellMoments<R> collide(R (&f)[qof(D)], R rho
             if (cz == 1) cu = cu + m.u[2];
             if (cz == -1) cu = cu - m.u[2];
             const R h = fma_r(cu, fma_r(R(4.5), cu, R(3)), mh);
-            f[i] = fma_r(omw[wclass<D>(i)], fma_r(m.rho, h, drho), keep * f[i]);
+            f[i] = fma_r(wr[wclass<D>(i)], h, fma_r(keep, f[i], wd[wclass<D>(i)]));
         }
     } else {
         R dm[3], d0[3], dp[3], key[3];
-#pragma unroll
-        for (int a = 0; a < D; ++a) axis_factors<EQ>(m.u[a], dm[a], d0[a], dp[a], key[a]);
+        all_axis_factors<D, EQ>(m.u, dm, d0, dp, key);
         R kmax = fmax(key[0], key[1]);
         if constexpr (D == 3) kmax = fmax(kmax, key[2]);
         const R om = collision_rate<EQ, BULK, R>(kmax, omega0, six_nu);
         const R keep = R(1) - om;
+        // per weight class: 2beta w rho and 2beta w drho, so that each direction costs
+        // two FMAs after its h: f* = (2beta w rho) h + ((1 - 2beta) f + 2beta w drho)
         const R omw[4] = {om * R(kW0), om * R(kW1), om * R(kW2), om * R(kW3)};
+        const R wr[4] = {omw[0] * m.rho, omw[1] * m.rho, omw[2] * m.rho, omw[3] * m.rho};
+        const R wd[4] = {omw[0] * drho, omw[1] * drho, omw[2] * drho, omw[3] * drho};
         const R dx[3] = {dm[0], d0[0], dp[0]};
         const R dy[3] = {dm[1], d0[1], dp[1]};
         const R tx[3] = {R(1) + dm[0], R(1) + d0[0], R(1) + dp[0]};
@@ -285,7 +332,7 @@ __host__ __device__ __forceinline__ CellMoments<R> collide(R (&f)[qof(D)], R rho
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const R h = fma_r(dy[cyo(i) + 1], tx[cxo(i) + 1], dx[cxo(i) + 1]);
-                f[i] = fma_r(omw[wclass<D>(i)], fma_r(m.rho, h, drho), keep * f[i]);
+                f[i] = fma_r(wr[wclass<D>(i)], h, fma_r(keep, f[i], wd[wclass<D>(i)]));
             }
         } else {
             const R ty[3] = {R(1) + dm[1], R(1) + d0[1], R(1) + dp[1]};
@@ -299,7 +346,7 @@ __host__ __device__ __forceinline__ CellMoments<R> collide(R (&f)[qof(D)], R rho
                 for (int q = 0; q < 3; ++q) {
                     const int i = p + 9 * q;
                     const R h = fma_r(dz[q], txy, exy);
-                    f[i] = fma_r(omw[wclass<D>(i)], fma_r(m.rho, h, drho), keep * f[i]);
+                    f[i] = fma_r(wr[wclass<D>(i)], h, fma_r(keep, f[i], wd[wclass<D>(i)]));
                 }
             }
         }

@@ -114,6 +114,56 @@ def test_fp64_parity_all_paths(D, dims, shape, eq, bulk):
     assert max_rel(got, ref) <= 1e-12
 
 
+# Launch shapes of the reduced-precision TMA kernels (rows must be 16-byte multiples):
+# whole rows with several rows per job and y wrap, and aligned segments with halos and a
+# shorter last segment.
+RP_SHAPES = [
+    (2, (40, 18, 1), (2, 256, 3, 4, 40, 2048)),
+    (2, (40, 18, 1), (2, 128, 2, 1, 16, 1024)),
+    (3, (24, 10, 6), (2, 128, 3, 3, 24, 1024)),
+    (3, (24, 10, 6), (2, 256, 2, 1, 8, 1024)),
+]
+
+
+@pytest.mark.parametrize("D,dims,shape", RP_SHAPES)
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("eq", [core.EQ_ENTROPIC, core.EQ_POLY2, core.EQ_PRODUCT])
+@pytest.mark.parametrize("bulk", [0, 1])
+def test_reduced_precision_tma_shapes(D, dims, shape, prec, eq, bulk):
+    """FP32 and binary16 storage through every TMA job layout, after an even and two odd
+    numbers of steps.  The TMA kernel and the one-cell-per-thread kernel evaluate the same
+    collision on the same stored values, so their stored states must agree bit for bit
+    (this checks the data movement of every layout: rows, y wrap, segments and their
+    halos, paired binary16 accesses); the velocity field must match the oracle within the
+    reduced-precision tolerance (relative L2 1e-4 for FP32, 1e-3 for binary16)."""
+    lbm = lbm_mod()
+    rho, u = inputs.random_state(D, dims, seed=300 + 11 * eq + 3 * bulk + D + prec, u_max=0.12)
+    tau = 0.57
+    lats = []
+    for sh in (shape, (1, 128)):
+        lat = lbm.Lattice(lbm.D2Q9 if D == 2 else lbm.D3Q27, dims, tau, eq, bulk, prec)
+        lat.set_launch_shape(*sh)
+        lat.init_fields(rho, u)
+        lats.append(lat)
+    assert lats[0].launch_info()["kernel"] == 2 and lats[1].launch_info()["kernel"] == 1
+    ref = core.init(D, dims, eq, rho, u)
+    done = 0
+    for n in (2, 3, 5):
+        for lat in lats:
+            lat.step(n - done)
+        ref = core.step(D, dims, eq, bulk, tau, n - done, ref)
+        done = n
+        a, b = (lat.get_populations("storage") for lat in lats)
+        diff = np.argwhere(a.view(np.uint8) != b.view(np.uint8))
+        assert diff.size == 0, f"after {n} steps the TMA and one-cell kernels differ at {diff[:4].tolist()}"
+        _, ug = core.moments(D, dims, lats[0].get_populations())
+        _, ur = core.moments(D, dims, ref)
+        err = rel_l2(ug, ur)
+        assert err <= {1: 1e-4, 2: 1e-3}[prec], f"after {n} steps rel-L2 velocity error {err:.3e}"
+    for lat in lats:
+        lat.close()
+
+
 def test_init_and_moments_fp64():
     """f = f^eq(rho, u) at t = 0 and the exported moments match the oracle."""
     lbm = lbm_mod()
