@@ -58,6 +58,29 @@ def taylor_green_3d_fields(n, u0=0.1, rho0=1.0, cs2=1.0 / 3.0):
     return rho_fn, u_fn
 
 
+def taylor_green_3d_torch(n, u0=0.1, rho0=1.0, device="cuda", slab=64):
+    """The 3-D Taylor-Green fields of `taylor_green_3d_fields` as float32 device tensors
+    (rho flat, u of shape (3, n^3), x fastest), built one slab of z-planes at a time in
+    float64 so that lattices of billions of cells need no host copy and no full-size
+    float64 temporaries."""
+    import torch
+    h = 2 * math.pi / n
+    t = torch.arange(n, device=device, dtype=torch.float64) * h
+    s, c, c2 = torch.sin(t), torch.cos(t), torch.cos(2 * t)
+    rho = torch.empty(n ** 3, device=device, dtype=torch.float32)
+    u = torch.zeros(3, n ** 3, device=device, dtype=torch.float32)
+    plane = n * n
+    for z0 in range(0, n, slab):
+        z1 = min(n, z0 + slab)
+        cz, c2z = c[z0:z1, None, None], c2[z0:z1, None, None]
+        sl = slice(z0 * plane, z1 * plane)
+        u[0, sl] = (u0 * cz * c[None, :, None] * s[None, None, :]).reshape(-1)
+        u[1, sl] = (-u0 * cz * s[None, :, None] * c[None, None, :]).reshape(-1)
+        rho[sl] = (rho0 + rho0 * u0 * u0 * 3.0 / 16.0 * (c2[None, None, :] + c2[None, :, None])
+                   * (c2z + 2.0)).reshape(-1)
+    return rho, u
+
+
 def taylor_green_3d(n, u0=0.1, rho0=1.0, dtype=np.float64):
     """Full 3-D Taylor-Green fields as flat arrays (separable evaluation)."""
     h = 2 * math.pi / n

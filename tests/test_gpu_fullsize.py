@@ -12,7 +12,9 @@ Tolerances for stored binary16 / FP32 values: each storage rounding moves f - w 
 at most half an ulp (u = 2^-11 resp. 2^-24 relative); a sampled value after n steps has
 been rounded n + 1 times directly and reaches other directions through rho and u, so
 |f_gpu - f_ref| <= (n + 2) u (|f_i - w_i| + w_i sum_j |f_j - w_j|) + n 2e-7 w_i, the last
-term for the FP32 collision arithmetic.
+term for the FP32 collision arithmetic.  Shifted values below 2^-14 are binary16
+subnormals, rounded to a multiple of 2^-24: each such store adds an absolute error of up
+to 2^-25, directly and through rho and u, hence a further (n + 2) 2^-25 (1 + Q w_i).
 """
 import math
 
@@ -25,6 +27,9 @@ from paper_2303_08163_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 UNIT = {1: 2.0 ** -24, 2: 2.0 ** -11}
+# half the spacing of the subnormal numbers: below 2^-14 a binary16 store rounds to a
+# multiple of 2^-24, an absolute error of up to 2^-25 that no relative bound covers
+FLOOR = {1: 0.0, 2: 2.0 ** -25}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -58,7 +63,7 @@ def check_sampled(lat, D, dims, eq, bulk, tau, prec, rho_fn, u_fn, nsteps, cells
     # storage roundings of this population plus those reaching it through rho and u
     # (bounded by the cell's total shifted magnitude), plus FP32 arithmetic per step
     tol = ((nsteps + 2) * UNIT[prec] * (shifted + w * shifted.sum(axis=1, keepdims=True))
-           + nsteps * 2e-7 * w)
+           + (nsteps + 2) * FLOOR[prec] * (1 + w * len(w)) + nsteps * 2e-7 * w)
     bad = np.abs(got - ref) > tol
     assert not bad.any(), f"{bad.sum()} sampled populations off; worst {np.max(np.abs(got - ref) - tol):.3e}"
 
@@ -152,3 +157,34 @@ def test_batch_4096_sampled_instances():
         assert float(np.max(np.abs(gk - fk) / np.abs(fk))) <= 1e-12
         assert np.all(np.abs(series[k] - sk) <= 1e-12 * np.abs(sk) + 1e-13 * int(c1 - c0))
     b.close()
+
+
+@pytest.mark.parametrize("shape", [(2, 256, 2, 1, 1304, 4096), (1, 256)])
+def test_lattice_over_2_31_cells(shape):
+    """The largest lattice the 280 GB of HBM holds comfortably: 1304^3 = 2.22e9 cells
+    (more than 2^31), 120 GB of binary16 populations.  Cell and population indices exceed
+    32 bits, so this checks the 64-bit indexing of the initialisation, of the TMA step
+    (whole 2608-byte rows, one per job) and of the one-cell step, and the sampled export,
+    against the oracle on sampled cells after an even and an odd number of steps."""
+    import torch
+    from paper_2303_08163_gb300 import lbm
+    n, u0 = 1304, 0.1
+    assert n ** 3 > 2 ** 31
+    tau = 0.5 + 3 * u0 * (n / (2 * math.pi)) / 1600.0
+    dims = (n, n, n)
+    rho, u = inputs.taylor_green_3d_torch(n, u0=u0, device="cuda")
+    rho_fn, u_fn = inputs.taylor_green_3d_fields(n, u0=u0)
+    lat = lbm.Lattice(lbm.D3Q27, dims, tau, lbm.ENTROPIC, 0, lbm.F16S)
+    lat.set_launch_shape(*shape)
+    lat.init_fields(rho, u, dtype=np.float32)
+    del rho, u
+    torch.cuda.empty_cache()
+    assert lat.launch_info()["kernel"] == shape[0]
+    cells = sample_cells(dims, 32, seed=13)
+    cells[-1] = (n - 1, n - 1, n - 1)  # the last cell: index n^3 - 1 > 2^31
+    lat.step(1)
+    check_sampled(lat, 3, dims, core.EQ_ENTROPIC, 0, tau, 2, rho_fn, u_fn, 1, cells)
+    lat.step(1)
+    check_sampled(lat, 3, dims, core.EQ_ENTROPIC, 0, tau, 2, rho_fn, u_fn, 2, cells)
+    lat.close()
+    torch.cuda.empty_cache()
