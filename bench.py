@@ -42,18 +42,18 @@ METRIC = "GLUPS and % of HBM roofline; FP16-store vs FP32/FP64 at stated L2 velo
 
 def fp64_flops_per_cell(eq, bulk):
     """Algorithmic FP64 flops of one D2Q9 collision as the kernels write it (an FMA is two
-    flops, a division or a square root one).  Common part 29: moments 18 (15 adds, one
-    division, two multiplies), drho 1, and the rate terms 10 (1 - 2beta and, per weight
-    class, 2beta w, 2beta w rho, 2beta w drho).  Entropic: per axis u^2, S and 1 + S
-    (2 x 5), one shared reciprocal of (1 + S_x)(1 + S_y) and its two cofactors (4), per
-    axis S - 1, d(+1) and d(-1) (2 x 8), t = 1 + d 3, per direction h and the relaxation
-    9 x 6.  Quadratic: u^2 3, -3/2 u^2 1,
-    the diagonal sums 2, per direction 9 x 8.  Product form: per-axis factors 2 x 7,
+    flops, a division or a square root one).  Entropic: the moment sums 15, rho^2 1, per
+    axis 3j, T = sqrt(rho^2 + 3j^2) and q = rho + T (2 x 5), the one division of
+    rho q_x q_y with its products (4), per axis u, S - 1, 3u, d(+1), d(-1) (2 x 9), drho 1,
+    the rate terms 10 (1 - 2beta and, per weight class, 2beta w, 2beta w rho, 2beta w drho),
+    t = 1 + d 3, per direction h and the relaxation 9 x 6.  Quadratic: moments 18 (the sums,
+    1/rho, two products), drho 1, rate terms 10, u^2 3, -3/2 u^2 1, the diagonal sums 2,
+    9 x 8.  Product form: moments 18, drho 1, rate terms 10, per-axis factors 2 x 7,
     t = 1 + d 3, 9 x 6.  The bulk correction adds the rate formula (6 entropic, 5
     otherwise)."""
-    base = 18 + 1 + 10
     if eq == 0:
-        return base + 30 + 3 + 54 + (6 if bulk else 0)
+        return 15 + 1 + 10 + 4 + 18 + 1 + 10 + 3 + 54 + (6 if bulk else 0)
+    base = 18 + 1 + 10
     if eq == 1:
         return base + 3 + 1 + 2 + 72 + (5 if bulk else 0)
     return base + 14 + 3 + 54 + (5 if bulk else 0)

@@ -239,11 +239,10 @@ __host__ __device__ __forceinline__ R equilibrium_h(const R (&u)[3], R (&h)[qof(
     }
 }
 
-// Moments of one cell from shifted populations.  The partial sums follow the tensor
-// structure of the lattice (first over c_z, then c_y, then c_x).
+// Density and momentum of one cell from shifted populations.  The partial sums follow the
+// tensor structure of the lattice (first over c_z, then c_y, then c_x).
 template <int D, typename R>
-__host__ __device__ __forceinline__ CellMoments<R> moments_shifted(const R (&f)[qof(D)], R rho0) {
-    CellMoments<R> m;
+__host__ __device__ __forceinline__ void moment_sums(const R (&f)[qof(D)], R rho0, R &rho, R (&j)[3]) {
     R a[9], bz[9];
     if constexpr (D == 2) {
 #pragma unroll
@@ -259,18 +258,71 @@ __host__ __device__ __forceinline__ CellMoments<R> moments_shifted(const R (&f)[
     const R c1 = (a[1] + a[4]) + a[7];  // c_x = 0
     const R c2 = (a[2] + a[5]) + a[8];  // c_x = +1
     const R rt = (c0 + c1) + c2;
-    const R jx = c2 - c0;
-    const R jy = ((a[6] + a[7]) + a[8]) - ((a[0] + a[1]) + a[2]);
-    R jz = R(0);
+    j[0] = c2 - c0;
+    j[1] = ((a[6] + a[7]) + a[8]) - ((a[0] + a[1]) + a[2]);
+    j[2] = R(0);
     if constexpr (D == 3) {
-        jz = ((bz[0] + bz[1]) + (bz[2] + bz[3])) + ((bz[4] + bz[5]) + (bz[6] + bz[7])) + bz[8];
+        j[2] = ((bz[0] + bz[1]) + (bz[2] + bz[3])) + ((bz[4] + bz[5]) + (bz[6] + bz[7])) + bz[8];
     }
-    m.rho = rho0 + rt;
+    rho = rho0 + rt;
+}
+
+// Moments of one cell from shifted populations: rho and u = j / rho.
+template <int D, typename R>
+__host__ __device__ __forceinline__ CellMoments<R> moments_shifted(const R (&f)[qof(D)], R rho0) {
+    CellMoments<R> m;
+    R jv[3];
+    moment_sums<D, R>(f, rho0, m.rho, jv);
+    const R jx = jv[0], jy = jv[1], jz = jv[2];
     const R inv = div_r(R(1), m.rho);
     m.u[0] = jx * inv;
     m.u[1] = jy * inv;
     m.u[2] = jz * inv;
     return m;
+}
+
+// FP64 entropic collisions: the moments and the per-axis factors with one IEEE division.
+// With T_a = rho S_a = sqrt(rho^2 + 3 j_a^2) and q_a = rho + T_a = rho (1 + S_a), the
+// identities 1/rho = (prod_a q_a) / (rho prod_a q_a) and S_a - 1 = 3 u_a^2 / (1 + S_a) =
+// 3 j_a^2 / (rho q_a) let one reciprocal of rho prod_a q_a serve 1/rho and every axis
+// (exact rewrites, a few ulp apart from the separate divisions).
+template <int D, typename R>
+__host__ __device__ __forceinline__ void entropic_factors_one_division(
+    const R (&f)[qof(D)], R rho0, CellMoments<R> &m, R (&dm)[3], R (&d0)[3], R (&dp)[3], R (&key)[3]) {
+    R j[3];
+    moment_sums<D, R>(f, rho0, m.rho, j);
+    const R rho = m.rho, rho2 = rho * rho;
+    R j3[3], T[3], q[3], cof[3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        j3[a] = R(3) * j[a];
+        T[a] = sqrt_r(fma_r(j3[a], j[a], rho2));
+        q[a] = rho + T[a];
+    }
+    R qprod;
+    if constexpr (D == 2) {
+        cof[0] = q[1];
+        cof[1] = q[0];
+        qprod = q[0] * q[1];
+    } else {
+        cof[0] = q[1] * q[2];
+        cof[1] = q[0] * q[2];
+        cof[2] = q[0] * q[1];
+        qprod = q[0] * cof[0];
+    }
+    const R r = R(1) / (rho * qprod);
+    const R irho = r * qprod;
+    m.u[2] = R(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        m.u[a] = j[a] * irho;
+        const R sm1 = (j3[a] * j[a]) * (r * cof[a]);  // S - 1 without cancellation
+        const R u3 = j3[a] * irho;
+        d0[a] = -sm1;
+        dp[a] = fma_r(R(2), sm1, u3);
+        dm[a] = fma_r(R(2), sm1, -u3);
+        key[a] = T[a] * irho;
+    }
 }
 
 // The fused collision of one cell, in place on shifted populations.  Returns the
@@ -283,7 +335,14 @@ __host__ __device__ __forceinline__ CellMoments<R> collide(R (&f)[qof(D)], R rho
     // weights per number of nonzero velocity components, folded at compile time
     constexpr double kW0 = wclass_weight<D>(0), kW1 = wclass_weight<D>(1);
     constexpr double kW2 = wclass_weight<D>(2), kW3 = wclass_weight<D>(D >= 3 ? 3 : 0);
-    const CellMoments<R> m = moments_shifted<D, R>(f, rho0);
+    CellMoments<R> m;
+    R dm[3], d0[3], dp[3], key[3];  // per-axis factors (entropic and product forms)
+    if constexpr (EQ == EQ_ENT && sizeof(R) == 8) {
+        entropic_factors_one_division<D, R>(f, rho0, m, dm, d0, dp, key);
+    } else {
+        m = moments_shifted<D, R>(f, rho0);
+        if constexpr (EQ != EQ_POLY2) all_axis_factors<D, EQ>(m.u, dm, d0, dp, key);
+    }
     const R drho = m.rho - rho0;
     if constexpr (EQ == EQ_POLY2) {
         R uu = m.u[0] * m.u[0] + m.u[1] * m.u[1];
@@ -314,8 +373,6 @@ __host__ __device__ __forceinline__ CellMoments<R> collide(R (&f)[qof(D)], R rho
             f[i] = fma_r(wr[wclass<D>(i)], h, fma_r(keep, f[i], wd[wclass<D>(i)]));
         }
     } else {
-        R dm[3], d0[3], dp[3], key[3];
-        all_axis_factors<D, EQ>(m.u, dm, d0, dp, key);
         R kmax = fmax(key[0], key[1]);
         if constexpr (D == 3) kmax = fmax(kmax, key[2]);
         const R om = collision_rate<EQ, BULK, R>(kmax, omega0, six_nu);
