@@ -281,6 +281,30 @@ def test_shear_wave_decay_at_rest():
     assert abs(rate / (nu * k * k) - 1.0) < 0.01
 
 
+@pytest.mark.parametrize("D", [2, 3])
+def test_diagnostics_closed_form(D):
+    """Diagnostics of f = f^eq(rho = 1, u) for the Taylor-Green velocity on an n^D grid
+    (the equilibrium reproduces rho and rho u exactly): mass n^D, momentum 0 (the field
+    is odd), kinetic energy 1/2 sum |u|^2 = u0^2 n^2 / 4 in 2-D and u0^2 n^3 / 8 in 3-D
+    (the mean of sin^2 cos^2 products), max |u_a| = u0 (reached where x = pi/2, y = z = 0)."""
+    n, u0 = 16, 0.07
+    if D == 2:
+        _, u = inputs.taylor_green_2d(n, u0=u0)
+        dims = (n, n, 1)
+        expect_ke = u0 * u0 * n ** 2 / 4
+    else:
+        _, u = inputs.taylor_green_3d(n, u0=u0)
+        dims = (n, n, n)
+        expect_ke = u0 * u0 * n ** 3 / 8
+    rho = np.ones(int(np.prod(dims)))
+    for eq in (core.EQ_ENTROPIC, core.EQ_POLY2, core.EQ_PRODUCT):
+        d = core.diagnostics(D, dims, core.init(D, dims, eq, rho, u))
+        assert abs(d["mass"] - np.prod(dims)) < 1e-11
+        assert np.all(np.abs(d["momentum"]) < 1e-12)
+        assert abs(d["kinetic"] / expect_ke - 1) < 1e-12
+        assert abs(d["max_u"] - u0) < 1e-15
+
+
 def test_probe_of_sine_density():
     """sum_x (1 + a sin(2 pi n x / N)) exp(-i 2 pi n x / N) = -i a N / 2 per row."""
     nx, ny, a = 48, 3, 1e-3
