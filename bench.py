@@ -8,7 +8,7 @@ step is one lattice time step of the whole grid.  Prints one JSON line.
   python bench.py [--gpus N] [--steps K] [--warmup W]
                   [--workload tgv3d|shear2d|tgv2d|batch|turb3d]
                   [--precision f16s|f32|f64] [--impl reference]
-  python bench.py --accuracy [--workload tgv3d|shear2d|turb3d] [--long-steps S]
+  python bench.py --accuracy [--workload tgv3d|shear2d|turb3d|batch] [--long-steps S]
 
 --accuracy prints the long accuracy checks instead of a bench line: on the Taylor-Green
 vortex the FP32 and binary16 velocity error against FP64 storage after four convective
@@ -366,6 +366,12 @@ def run_native(args):
     stream = torch.cuda.current_stream()
     w = workload(args)
     if w["dims"] is None:
+        if args.accuracy:
+            if rank == 0:
+                steps = args.long_steps or 4000
+                res = [batch_mode_sweep(lbm, eq, args.bulk, steps=steps) for eq in (0, 1)]
+                print(json.dumps({"accuracy": res, "workload": w["name"]}), flush=True)
+            return
         return run_batch(args, w, torch, lbm, dev, rank, ws)
     D, dims, prec = w["D"], w["dims"], w["prec"]
     Q = 3 ** D
@@ -653,6 +659,91 @@ def compare_precisions(torch, lbm, dev, w, args, rho, u):
             lat.close()
             torch.cuda.empty_cache()
     return out
+
+
+def batch_mode_sweep(lbm, eq, bulk, steps=4000, every=10, skip_steps=200):
+    """The batched linear-mode sweep at full size (4096 instances, `steps` steps, probes
+    every `every` steps), checked instance by instance against the scheme's linear theory:
+    after `skip_steps` (the non-hydrodynamic transients), each probe series is fitted by a
+    least-squares linear map (the shear wave on j_y, the two acoustic modes on rho and j_x)
+    and every fitted per-sample multiplier is compared with the nearest lambda^K of the
+    von Neumann matrix M = E (delta + J) at the instance's (tau, U0, k) from the library's
+    eigen-solver.  The fit window holds the samples after `skip_steps` whose signal stays
+    within 1e-9 .. 1e3 of the initial amplitude; instances with fewer than 8 samples in it
+    (strongly damped waves) are counted, not fitted."""
+    from paper_2303_08163_gb300 import fits, inputs
+    table = inputs.linear_mode_batch(count=4096, seed=2303)
+    count = len(table["nx"])
+    dims = np.stack([table["nx"], table["ny"], np.ones(count, dtype=np.int32)], axis=1)
+    fields = [inputs.linear_mode_fields(table, k) for k in range(count)]
+    rho = np.concatenate([f[0] for f in fields])
+    u = np.concatenate([f[1].reshape(-1) for f in fields])
+    kvec = np.stack([table["nmode"], np.zeros(count, np.int32), np.zeros(count, np.int32)], axis=1)
+    b = lbm.Batch(lbm.D2Q9, dims, table["tau"], eq, bulk)
+    b.init_fields(rho, u)
+    b.set_probe(kvec, every)
+    t0 = time.time()
+    b.step(steps)
+    b.sync()
+    run_s = time.time() - t0
+    series = b.probe_series()
+    status = b.status()
+    b.close()
+    k = 2 * math.pi * table["nmode"] / table["nx"]
+    params = np.stack([table["tau"], np.ones(count), table["U0"], np.zeros(count), k, np.zeros(count)], axis=1)
+    lam = lbm.vn_eigenvalues(eq, bulk, params)
+    unstable = np.abs(lam[:, 0]) > 1 + 1e-12
+    s0 = skip_steps // every
+    errs, ks, short, nonfinite = [], [], 0, 0
+    worst = None
+    for i in range(count):
+        chans = [2] if table["kind"][i] == 0 else [0, 1]
+        ref = float(np.linalg.norm(series[i, 0, chans]))  # the initial amplitude
+        x = series[i, s0:, :][:, chans]
+        if not np.all(np.isfinite(x)):
+            good = np.all(np.isfinite(x), axis=1)
+            x = x[:np.argmin(good)] if not good.all() else x
+            nonfinite += 1
+        mag = np.linalg.norm(x, axis=1)
+        if len(mag) == 0 or ref == 0:
+            short += 1
+            continue
+        # fit while the signal stays within 1e-9 .. 1e3 of the initial amplitude (the
+        # probe's round-off floor is about 1e-12 of it)
+        inside = (mag > 1e-9 * ref) & (mag < 1e3 * ref)
+        n = int(np.argmin(inside)) if not inside.all() else len(mag)
+        if n < 8:
+            short += 1
+            continue
+        mu = fits.mode_multipliers(x[:n], nmodes=len(chans))
+        target = lam[i] ** every
+        for m in mu:
+            e = float(np.min(np.abs(target - m)))
+            errs.append(e)
+            ks.append(k[i])
+            if worst is None or e > worst[0]:
+                worst = (e, i)
+    errs, ks = np.array(errs), np.array(ks)
+
+    def stats(sel):
+        e = errs[sel]
+        return {"compared": int(len(e)), "median": float(np.median(e)) if len(e) else None,
+                "p99": float(np.quantile(e, 0.99)) if len(e) else None, "max": float(e.max()) if len(e) else None}
+    wi = worst[1] if worst else None
+    return {"equilibrium": {0: "entropic", 1: "poly2", 2: "product"}[eq], "bulk_corr": bulk,
+            "instances": count, "steps": steps, "every": every, "run_seconds": run_s,
+            "linearly_unstable_by_von_neumann": int(unstable.sum()),
+            "instances_with_nonfinite_probe": int(nonfinite), "batch_status_nonfinite": int((status > 0).sum()),
+            "instances_fitted": int(count - short), "too_fast_to_fit": int(short),
+            "multipliers_compared": int(len(errs)),
+            "abs_error_median": float(np.median(errs)) if len(errs) else None,
+            "abs_error_p99": float(np.quantile(errs, 0.99)) if len(errs) else None,
+            "abs_error_max": float(errs.max()) if len(errs) else None,
+            "abs_error_k_le_pi_4": stats(ks <= math.pi / 4 + 1e-12),
+            "abs_error_k_gt_pi_4": stats(ks > math.pi / 4 + 1e-12),
+            "worst_instance": None if wi is None else {
+                "tau": float(table["tau"][wi]), "U0": float(table["U0"][wi]), "nx": int(table["nx"][wi]),
+                "nmode": int(table["nmode"][wi]), "kind": int(table["kind"][wi])}}
 
 
 def run_batch(args, w, torch, lbm, dev, rank, ws):
