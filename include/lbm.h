@@ -84,7 +84,9 @@ enum lbm_status {
     LBM_ECUDA = -3,      /* a CUDA runtime call or kernel launch failed */
     LBM_ENONFINITE = -4, /* fused diagnostics saw a non-finite mass or momentum */
     LBM_ETIMEOUT = -5,   /* a bounded device wait ran out; the kernel returned early */
-    LBM_ESTATE = -6      /* object is in an error state or the call is out of order */
+    LBM_ESTATE = -6,     /* object is in an error state or the call is out of order */
+    LBM_ECHECK = -7      /* checked builds only (compiled with -DLBM_CHECKED): a device-side
+                            bounds or alignment check failed and the access was skipped */
 };
 
 /* Options for lbm_set_option. */

@@ -15,6 +15,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbm.so")
+# the checked variant (-DLBM_CHECKED: device-side bounds and alignment checks that report
+# LBM_ECHECK instead of faulting), for tests; never the default library
+CHECKED_DIR = os.path.join(HERE, "_build_checked")
+CHECKED_LIB = os.path.join(CHECKED_DIR, "liblbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -46,17 +50,21 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force=False, verbose=False, jobs=None, extra_flags=()):
-    """Compile and link liblbm.so if any source is newer; return its path."""
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force=False, verbose=False, jobs=None, extra_flags=(), checked=False):
+    """Compile and link liblbm.so if any source is newer; return its path.  checked=True
+    builds the bounds-checked variant into _build_checked/ instead."""
+    out_dir, lib = (CHECKED_DIR, CHECKED_LIB) if checked else (OUT_DIR, LIB)
+    if checked:
+        extra_flags = tuple(extra_flags) + ("-DLBM_CHECKED",)
+    os.makedirs(out_dir, exist_ok=True)
     deps = _deps()
-    if not force and not _stale(LIB, deps):
-        return LIB
+    if not force and not _stale(lib, deps):
+        return lib
     nvcc = _nvcc()
     objs = []
     cmds = []
     for src in _sources():
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         cmds.append([nvcc] + _flags(extra_flags) + ["-c", src, "-o", obj])
 
@@ -74,13 +82,13 @@ def build(force=False, verbose=False, jobs=None, extra_flags=()):
                 errors.append(" ".join(cmd) + "\n" + r.stdout + r.stderr)
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     link = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

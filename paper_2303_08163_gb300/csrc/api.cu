@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lbm.h"
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
@@ -139,12 +141,15 @@ int ctx_sticky(lbm_ctx *c, int code) {
     return code;
 }
 
-// Device status word: LBM_ETIMEOUT if a kernel's bounded wait ran out.
+// Device status word: LBM_ETIMEOUT if a kernel's bounded wait ran out, LBM_ECHECK if a
+// bounds or alignment check of a checked build failed (the first error sticks).
 int read_status(lbm_ctx *c) {
     int32_t st = 0;
     cudaError_t e = cudaMemcpyAsync(&st, c->status, sizeof st, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return ctx_sticky(c, cuda_fail("status read", e));
+    if (st == LBM_ECHECK)
+        return ctx_sticky(c, fail(LBM_ECHECK, "a device bounds or alignment check failed (checked build)"));
     if (st != 0) return ctx_sticky(c, fail(LBM_ETIMEOUT, "a bounded device wait ran out (status %d)", st));
     return LBM_OK;
 }
@@ -442,6 +447,12 @@ int set_last_error(int code, const char *msg) {
 }
 }  // namespace lbmh
 
+// NVTX range around a public call (header-only NVTX: free unless a profiler is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 extern "C" {
 
 const char *lbm_last_error(void) { return g_err.c_str(); }
@@ -601,6 +612,7 @@ int lbm_init_fields(lbm_ctx *c, const void *rho, const void *u, int dtype, int o
 }
 
 int lbm_step(lbm_ctx *c, int64_t n) {
+    NvtxRange range("lbm_step");
     int rc = ctx_check(c);
     if (rc) return rc;
     if (n < 0) return fail(LBM_EINVAL, "n must be >= 0");
@@ -1180,6 +1192,7 @@ static int batch_reserve_series(lbm_batch *b, int64_t samples) {
 }
 
 int lbm_batch_step(lbm_batch *b, int64_t n) {
+    NvtxRange range("lbm_batch_step");
     int rc = batch_check(b);
     if (rc) return rc;
     if (n < 0) return fail(LBM_EINVAL, "n must be >= 0");

@@ -22,10 +22,17 @@ template <int D, int P, int EQ, bool BULK>
 __device__ __forceinline__ CellMoments<typename Storage<P>::R> aa_cell_step(
     typename Storage<P>::T *__restrict__ A, int64_t plane, int nx, int ny, int nz, int x, int y,
     int z, int odd, typename Storage<P>::R rho0, typename Storage<P>::R omega0,
-    typename Storage<P>::R six_nu) {
+    typename Storage<P>::R six_nu, int32_t *status = nullptr) {
     using St = Storage<P>;
     using R = typename St::R;
     constexpr int Q = qof(D);
+    // checked builds: the cell and (through the periodic wrap) all its neighbours lie
+    // inside the lattice, so every index below stays inside the Q planes
+    if (!LBM_CHECK(x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz &&
+                       (int64_t)nx * ny * nz <= plane, status)) {
+        CellMoments<R> none{};
+        return none;
+    }
     const int64_t cell = x + (int64_t)nx * (y + (int64_t)ny * z);
     const int xs[3] = {wrapi(x - 1, nx), x, wrapi(x + 1, nx)};
     const int ys[3] = {wrapi(y - 1, ny), y, wrapi(y + 1, ny)};
@@ -88,7 +95,7 @@ __global__ void __launch_bounds__(256) k_step_generic(const lbmh::StepArgs a) {
             z = (int)(rowi / ny);
         }
         const CellMoments<R> m = aa_cell_step<D, P, EQ, BULK>(A, a.lat.plane, nx, ny, nz, x, y, z,
-                                                              a.odd, rho0, omega0, six_nu);
+                                                              a.odd, rho0, omega0, six_nu, a.status);
         if (a.diag) {
             loc.add(m.rho, m.u, rho0);
             if (loc.count == 16) loc.flush(acc, a.rho0);

@@ -87,6 +87,24 @@ __device__ __forceinline__ uint32_t tma_job_bytes(const lbmh::StepArgs &a, const
     return bytes;
 }
 
+// Checked builds: a bulk copy of `bytes` between global `gp` and shared `sp` stays inside
+// the population array and the stage, and meets the 16-byte rules of cp.async.bulk.
+template <int D, typename T>
+__device__ __forceinline__ bool bulk_ok(const lbmh::StepArgs &a, const TmaGeom &g, const T *stage,
+                                        const T *sp, const T *gp, uint32_t bytes) {
+#ifdef LBM_CHECKED
+    constexpr int Q = qof(D);
+    const T *A0 = static_cast<const T *>(a.lat.A);
+    const int64_t n = (int64_t)bytes / (int64_t)sizeof(T);
+    const bool ok = bytes > 0 && (bytes & 15u) == 0 && ((uintptr_t)gp & 15u) == 0 &&
+                    (smem_u32(sp) & 15u) == 0 && gp >= A0 && gp + n <= A0 + (int64_t)Q * a.lat.plane &&
+                    sp >= stage && sp + n <= stage + (int64_t)Q * g.bufstride;
+    return LBM_CHECK(ok, a.status);
+#else
+    return true;
+#endif
+}
+
 // Loads of buffer b of a job into its stage (issued by producer lane b).
 template <int D, typename T>
 __device__ __forceinline__ void tma_issue_loads(const lbmh::StepArgs &a, const TmaGeom &g,
@@ -99,17 +117,20 @@ __device__ __forceinline__ void tma_issue_loads(const lbmh::StepArgs &a, const T
         const int ysrc = a.odd ? wrapi(j.y0 + r - cyo(b), ny) : j.y0 + r;
         const int run = min(j.nrows - r, ny - ysrc);
         const T *src = buffer_row<D, T>(a, b, j.z, j.y0 + r) + j.X0;
-        bulk_g2s(sbuf + r * g.rowstride + g.halo, src, (uint32_t)(run * j.len * (int)sizeof(T)), bar);
+        T *dst = sbuf + r * g.rowstride + g.halo;
+        const uint32_t bytes = (uint32_t)(run * j.len * (int)sizeof(T));
+        if (bulk_ok<D, T>(a, g, st, dst, src, bytes)) bulk_g2s(dst, src, bytes, bar);
         r += run;
     }
     if (a.odd && g.nseg > 1) {
         const T *grow = buffer_row<D, T>(a, b, j.z, j.y0);
         if (cxo(b) == 1) {
             const int xs = j.X0 == 0 ? nx - U : j.X0 - U;
-            bulk_g2s(sbuf, grow + xs, U * sizeof(T), bar);
+            if (bulk_ok<D, T>(a, g, st, sbuf, grow + xs, U * sizeof(T))) bulk_g2s(sbuf, grow + xs, U * sizeof(T), bar);
         } else if (cxo(b) == -1) {
             const int xs = (j.X0 + j.len == nx) ? 0 : j.X0 + j.len;
-            bulk_g2s(sbuf + g.halo + j.len, grow + xs, U * sizeof(T), bar);
+            T *dst = sbuf + g.halo + j.len;
+            if (bulk_ok<D, T>(a, g, st, dst, grow + xs, U * sizeof(T))) bulk_g2s(dst, grow + xs, U * sizeof(T), bar);
         }
     }
 }
@@ -127,16 +148,21 @@ __device__ __forceinline__ void tma_issue_stores(const lbmh::StepArgs &a, const 
             const int ysrc = a.odd ? wrapi(j.y0 + r - cyo(b), ny) : j.y0 + r;
             const int run = min(j.nrows - r, ny - ysrc);
             T *dst = buffer_row<D, T>(a, b, j.z, j.y0 + r) + j.X0;
-            bulk_s2g(dst, sbuf + r * g.rowstride + g.halo, (uint32_t)(run * j.len * (int)sizeof(T)));
+            const T *src = sbuf + r * g.rowstride + g.halo;
+            const uint32_t bytes = (uint32_t)(run * j.len * (int)sizeof(T));
+            if (bulk_ok<D, T>(a, g, st, src, dst, bytes)) bulk_s2g(dst, src, bytes);
             r += run;
         }
     } else {
         T *grow = buffer_row<D, T>(a, b, j.z, j.y0);
         if (cxo(b) == 0) {
-            bulk_s2g(grow + j.X0, sbuf + g.halo, (uint32_t)(j.len * (int)sizeof(T)));
+            const uint32_t bytes = (uint32_t)(j.len * (int)sizeof(T));
+            if (bulk_ok<D, T>(a, g, st, sbuf + g.halo, grow + j.X0, bytes)) bulk_s2g(grow + j.X0, sbuf + g.halo, bytes);
         } else if (j.len > U) {
             const int off = cxo(b) == 1 ? 0 : U;  // skip the ragged end the plain stores take
-            bulk_s2g(grow + j.X0 + off, sbuf + g.halo + off, (uint32_t)((j.len - U) * (int)sizeof(T)));
+            const uint32_t bytes = (uint32_t)((j.len - U) * (int)sizeof(T));
+            if (bulk_ok<D, T>(a, g, st, sbuf + g.halo + off, grow + j.X0 + off, bytes))
+                bulk_s2g(grow + j.X0 + off, sbuf + g.halo + off, bytes);
         }
     }
 }
@@ -162,7 +188,7 @@ __device__ __forceinline__ void tma_plain_stores(const lbmh::StepArgs &a, const 
             if (e == 0) { gx = (j.X0 + j.len == nx) ? 0 : j.X0 + j.len; sx = g.halo + j.len; }
             else { gx = j.X0 + e; sx = g.halo + e; }
         }
-        grow[gx] = srow[sx];
+        if (LBM_CHECK(gx >= 0 && gx < nx && sx >= 0 && sx < g.bufstride, a.status)) grow[gx] = srow[sx];
     }
 }
 
@@ -239,11 +265,14 @@ __device__ __forceinline__ void tma_compute(const lbmh::StepArgs &a, const TmaGe
     int xl = tid - r * j.len;
     for (int c = tid; c < ncells; c += nthr) {
         const CellPos p = cell_pos(g, r, xl, j.len);
-        R f[Q];
-        tma_load_cell<D, P, CAPB>(st, p, a.odd, f);
-        const CellMoments<R> m = collide<D, EQ, BULK, R>(f, rho0, omega0, six_nu);
-        tma_store_cell<D, P, CAPB>(st, p, a.odd, f);
-        if (a.diag) loc.add(m.rho, m.u, rho0);
+        // checked builds: every position the cell touches lies inside its direction buffer
+        if (LBM_CHECK(p.row + min(p.xm, p.x) >= 0 && p.row + max(p.xp, p.x) < g.bufstride, a.status)) {
+            R f[Q];
+            tma_load_cell<D, P, CAPB>(st, p, a.odd, f);
+            const CellMoments<R> m = collide<D, EQ, BULK, R>(f, rho0, omega0, six_nu);
+            tma_store_cell<D, P, CAPB>(st, p, a.odd, f);
+            if (a.diag) loc.add(m.rho, m.u, rho0);
+        }
         xl += nthr;
         while (xl >= j.len) {
             xl -= j.len;
@@ -293,78 +322,84 @@ __device__ __forceinline__ void tma_compute_pairs(const lbmh::StepArgs &a, const
         const int xb = (mode == 1 && xa + 1 == j.len) ? 0 : xa + 1;
         const int pm = xa - 1;
         const int pp = xb + 1;
-        float fa[Q], fb[Q];
-        if (mode == 0) {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const float2 v = ld_pair(row + i * bs, xa);
-                fa[i] = v.x;
-                fb[i] = v.y;
-            }
-        } else if (mode == 1) {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const __half *b = row + i * bs;
-                if (cxo(i) == 0) {
-                    fa[i] = __half2float(b[xa]);
-                    fb[i] = __half2float(b[xb]);
-                } else {
-                    const float2 v = ld_pair(b, cxo(i) == 1 ? pm : xb);
+        // checked builds: every position the pair touches lies inside its direction buffer
+        const int row_off = r * g.rowstride + g.halo;
+        const int lo = mode == 0 ? xa : min(min(pm, xa), xb);
+        const int hi = mode == 0 ? xa + 1 : max(max(xb + 1, pp), xa);
+        if (LBM_CHECK(row_off + lo >= 0 && row_off + hi < bs, a.status)) {
+            float fa[Q], fb[Q];
+            if (mode == 0) {
+    #pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const float2 v = ld_pair(row + i * bs, xa);
                     fa[i] = v.x;
                     fb[i] = v.y;
                 }
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const __half *b = row + i * bs;
-                if (cxo(i) == 0) {
-                    const float2 v = ld_pair(b, xa);
-                    fa[i] = v.x;
-                    fb[i] = v.y;
-                } else if (cxo(i) == 1) {
-                    fa[i] = __half2float(b[pm]);
-                    fb[i] = __half2float(b[xa]);
-                } else {
-                    fa[i] = __half2float(b[xb]);
-                    fb[i] = __half2float(b[pp]);
+            } else if (mode == 1) {
+    #pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const __half *b = row + i * bs;
+                    if (cxo(i) == 0) {
+                        fa[i] = __half2float(b[xa]);
+                        fb[i] = __half2float(b[xb]);
+                    } else {
+                        const float2 v = ld_pair(b, cxo(i) == 1 ? pm : xb);
+                        fa[i] = v.x;
+                        fb[i] = v.y;
+                    }
+                }
+            } else {
+    #pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const __half *b = row + i * bs;
+                    if (cxo(i) == 0) {
+                        const float2 v = ld_pair(b, xa);
+                        fa[i] = v.x;
+                        fb[i] = v.y;
+                    } else if (cxo(i) == 1) {
+                        fa[i] = __half2float(b[pm]);
+                        fb[i] = __half2float(b[xa]);
+                    } else {
+                        fa[i] = __half2float(b[xb]);
+                        fb[i] = __half2float(b[pp]);
+                    }
                 }
             }
-        }
-        const CellMoments<float> ma = collide<D, EQ, BULK, float>(fa, rho0, omega0, six_nu);
-        const CellMoments<float> mb = collide<D, EQ, BULK, float>(fb, rho0, omega0, six_nu);
-        if (mode == 0) {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) st_pair(row + (Q - 1 - i) * bs, xa, fa[i], fb[i]);
-        } else if (mode == 1) {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                __half *b = row + (Q - 1 - i) * bs;
-                if (cxo(i) == 0) {
-                    b[xa] = __float2half_rn(fa[i]);
-                    b[xb] = __float2half_rn(fb[i]);
-                } else {
-                    st_pair(b, cxo(i) == 1 ? xb : pm, fa[i], fb[i]);
+            const CellMoments<float> ma = collide<D, EQ, BULK, float>(fa, rho0, omega0, six_nu);
+            const CellMoments<float> mb = collide<D, EQ, BULK, float>(fb, rho0, omega0, six_nu);
+            if (mode == 0) {
+    #pragma unroll
+                for (int i = 0; i < Q; ++i) st_pair(row + (Q - 1 - i) * bs, xa, fa[i], fb[i]);
+            } else if (mode == 1) {
+    #pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    __half *b = row + (Q - 1 - i) * bs;
+                    if (cxo(i) == 0) {
+                        b[xa] = __float2half_rn(fa[i]);
+                        b[xb] = __float2half_rn(fb[i]);
+                    } else {
+                        st_pair(b, cxo(i) == 1 ? xb : pm, fa[i], fb[i]);
+                    }
+                }
+            } else {
+    #pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    __half *b = row + (Q - 1 - i) * bs;
+                    if (cxo(i) == 0) {
+                        st_pair(b, xa, fa[i], fb[i]);
+                    } else if (cxo(i) == 1) {
+                        b[xb] = __float2half_rn(fa[i]);
+                        b[pp] = __float2half_rn(fb[i]);
+                    } else {
+                        b[pm] = __float2half_rn(fa[i]);
+                        b[xa] = __float2half_rn(fb[i]);
+                    }
                 }
             }
-        } else {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                __half *b = row + (Q - 1 - i) * bs;
-                if (cxo(i) == 0) {
-                    st_pair(b, xa, fa[i], fb[i]);
-                } else if (cxo(i) == 1) {
-                    b[xb] = __float2half_rn(fa[i]);
-                    b[pp] = __float2half_rn(fb[i]);
-                } else {
-                    b[pm] = __float2half_rn(fa[i]);
-                    b[xa] = __float2half_rn(fb[i]);
-                }
+            if (a.diag) {
+                loc.add(ma.rho, ma.u, rho0);
+                loc.add(mb.rho, mb.u, rho0);
             }
-        }
-        if (a.diag) {
-            loc.add(ma.rho, ma.u, rho0);
-            loc.add(mb.rho, mb.u, rho0);
         }
         xh += nthr;
         while (xh >= hl) {
@@ -488,7 +523,7 @@ __global__ void __launch_bounds__(kTmaMaxThreads + 32) k_step_tma(const lbmh::St
             if (lane == 0) mbar_arrive_cta(&empty[s]);
         }
     }
-    if (failed && lane == 0) atomicExch(a.status, -5); /* LBM_ETIMEOUT */
+    if (failed && lane == 0) report_status(a.status, -5); /* LBM_ETIMEOUT */
     if (a.diag) diag_block_store(acc, a.partials + (int64_t)blockIdx.x * lbmh::kDiagWords);
 }
 

@@ -9,6 +9,23 @@ namespace lbmd {
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
+// The first error a kernel reports sticks in the device status word.
+__device__ __forceinline__ void report_status(int32_t *status, int32_t code) { atomicCAS(status, 0, code); }
+
+// Checked builds (-DLBM_CHECKED): device-side bounds and alignment checks.  A failed check
+// records LBM_ECHECK (-7) in the status word and the caller skips the access, so an
+// indexing mistake shows up as an error code instead of a memory fault.  In normal builds
+// every check is the constant true and compiles away.
+#ifdef LBM_CHECKED
+__device__ __forceinline__ bool lbm_check(bool ok, int32_t *status) {
+    if (!ok && status) report_status(status, -7);
+    return ok;
+}
+#define LBM_CHECK(ok, status) ::lbmd::lbm_check((ok), (status))
+#else
+#define LBM_CHECK(ok, status) true
+#endif
+
 // A per-step scalar in the collision precision (no FP64 conversion in FP32 kernels).
 template <typename R> __device__ __forceinline__ R step_scalar(double d, float f);
 template <> __device__ __forceinline__ double step_scalar<double>(double d, float) { return d; }

@@ -23,9 +23,9 @@ STORAGE_NUMPY = {0: np.float64, 1: np.float32, 2: np.float16}
 OPT_DIAG_EVERY, OPT_KERNEL, OPT_USE_GRAPH, OPT_TUNE = 0, 1, 2, 3
 KERNEL_AUTO, KERNEL_GENERIC, KERNEL_TMA = 0, 1, 2
 
-OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ESTATE, ECHECK = 0, -1, -2, -3, -4, -5, -6, -7
 STATUS_NAMES = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA",
-                -4: "LBM_ENONFINITE", -5: "LBM_ETIMEOUT", -6: "LBM_ESTATE"}
+                -4: "LBM_ENONFINITE", -5: "LBM_ETIMEOUT", -6: "LBM_ESTATE", -7: "LBM_ECHECK"}
 
 # Every symbol the header declares, with (restype, argtypes).
 _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
@@ -87,7 +87,8 @@ class LBMError(RuntimeError):
 
 
 def library_path():
-    return _build.LIB
+    """The in-tree liblbm.so; LBM_LIBRARY names another in-tree build (the checked one)."""
+    return os.environ.get("LBM_LIBRARY") or _build.LIB
 
 
 def load():
