@@ -7,14 +7,22 @@ autotuned one), on outputs the oracle can compute one by one:
 - D2Q9 4096^2 double shear layer, FP32: sampled cells after 1 and 2 steps.
 - 4096 batched D2Q9 instances (FP64): probe series and final populations of sampled
   instances equal the oracle's to 1e-12.
+- D3Q27 1024 x 512 x 512 decaying turbulence, binary16 and FP32: sampled cells after 1 and
+  2 steps.
+- The largest lattice: 1304^3 cells (more than 2^31), binary16, both step kernels.
 
 Tolerances for stored binary16 / FP32 values: each storage rounding moves f - w rho0 by
-at most half an ulp (u = 2^-11 resp. 2^-24 relative); a sampled value after n steps has
-been rounded n + 1 times directly and reaches other directions through rho and u, so
-|f_gpu - f_ref| <= (n + 2) u (|f_i - w_i| + w_i sum_j |f_j - w_j|) + n 2e-7 w_i, the last
-term for the FP32 collision arithmetic.  Shifted values below 2^-14 are binary16
-subnormals, rounded to a multiple of 2^-24: each such store adds an absolute error of up
-to 2^-25, directly and through rho and u, hence a further (n + 2) 2^-25 (1 + Q w_i).
+at most half an ulp (u = 2^-11 resp. 2^-24 relative; below 2^-14 a binary16 value is a
+subnormal, rounded to a multiple of 2^-24, an absolute error of up to 2^-25).  A sampled
+value after n steps has been rounded n + 1 times directly; the roundings of the other
+populations reach it through rho and u, to first order amplified by at most omega K
+(omega = 1/tau, K the bound of `sensitivity` on |d f^eq_i / d f_j| / w_i at the field's
+largest |u_a|); the FP32 collision is a chain of at most 32 roundings of operands bounded
+by w_i (1 + S).  So, with S = sum_j |f_j - w_j|,
+|f_gpu - f_ref| <= (n + 2) [u (|f_i - w_i| + omega K w_i S) + 2^-25 (1 + omega K Q w_i)]
+                   + 32 n 2^-24 w_i (1 + S) (1 + omega K)
+(the 2^-25 term for binary16 only).  Data-movement errors (a wrong neighbour, direction or
+layout) are of order w_i |u| and stay well outside this bound.
 """
 import math
 
@@ -55,15 +63,30 @@ def flat(cells, dims):
     return cells[:, 0] + nx * (cells[:, 1] + ny * cells[:, 2])
 
 
-def check_sampled(lat, D, dims, eq, bulk, tau, prec, rho_fn, u_fn, nsteps, cells):
+def sensitivity(D, umax, rho_min=0.9):
+    """Bound K on |d f^eq_i / d f_j| / w_i for |u_a| <= umax, rho >= rho_min: f^eq_i =
+    w_i rho (1 + h_i(u)) with u = j / rho, so a change of f_j moves f^eq_i through rho
+    (factor 1 + |h_i|) and through u (factor sum_a |dh_i/du_a| (1 + |u_a|) / rho).  For the
+    entropic and product forms h_i = prod_a t_a - 1 with t <= 1 + 3u + 3u^2 and |dt/du| <=
+    3 + 6u; for the quadratic form |dh/du_a| <= 3 + 9 D u + 3u."""
+    t = 1 + 3 * umax + 3 * umax ** 2
+    hmax = max(t ** D - 1, 3 * D * umax + 4.5 * (D * umax) ** 2 + 1.5 * D * umax ** 2)
+    g = max((3 + 6 * umax) * t ** (D - 1), 3 + 9 * D * umax + 3 * umax)
+    return 1 + hmax + D * g * (1 + umax) / rho_min
+
+
+def check_sampled(lat, D, dims, eq, bulk, tau, prec, rho_fn, u_fn, nsteps, cells, umax):
     got = lat.sample_populations(flat(cells, dims))
     ref = core.local_populations(D, dims, eq, bulk, tau, nsteps, rho_fn, u_fn, cells)
     _, w = core.lattice(D)
     shifted = np.abs(ref - w)
-    # storage roundings of this population plus those reaching it through rho and u
-    # (bounded by the cell's total shifted magnitude), plus FP32 arithmetic per step
-    tol = ((nsteps + 2) * UNIT[prec] * (shifted + w * shifted.sum(axis=1, keepdims=True))
-           + (nsteps + 2) * FLOOR[prec] * (1 + w * len(w)) + nsteps * 2e-7 * w)
+    S = shifted.sum(axis=1, keepdims=True)
+    # storage roundings of this population, plus those reaching it through rho and u
+    # (first order, amplified by at most omega K), plus the FP32 collision arithmetic
+    ok = (1.0 / tau) * sensitivity(D, umax)
+    tol = ((nsteps + 2) * UNIT[prec] * (shifted + ok * w * S)
+           + (nsteps + 2) * FLOOR[prec] * (1 + ok * w * len(w))
+           + 32 * nsteps * 2.0 ** -24 * w * (1 + S) * (1 + ok))
     bad = np.abs(got - ref) > tol
     assert not bad.any(), f"{bad.sum()} sampled populations off; worst {np.max(np.abs(got - ref) - tol):.3e}"
 
@@ -85,9 +108,9 @@ def test_tgv_512_sampled_and_conservation(prec):
     lat.init_fields(rho, u)
     cells = sample_cells(dims, 48, seed=prec)
     lat.step(1)
-    check_sampled(lat, 3, dims, core.EQ_ENTROPIC, 0, tau, prec, rho_fn, u_fn, 1, cells)
+    check_sampled(lat, 3, dims, core.EQ_ENTROPIC, 0, tau, prec, rho_fn, u_fn, 1, cells, u0)
     lat.step(1)
-    check_sampled(lat, 3, dims, core.EQ_ENTROPIC, 0, tau, prec, rho_fn, u_fn, 2, cells)
+    check_sampled(lat, 3, dims, core.EQ_ENTROPIC, 0, tau, prec, rho_fn, u_fn, 2, cells, u0)
     d0 = lat.diagnostics()
     nsteps = 40
     lat.step(nsteps)
@@ -121,9 +144,9 @@ def test_shear_layer_4096_sampled():
         cells = sample_cells(dims, 48, seed=11)
         cells[:, 2] = 0
         lat.step(1)
-        check_sampled(lat, 2, dims, eq, 0, tau, 1, rho_fn, u_fn, 1, cells)
+        check_sampled(lat, 2, dims, eq, 0, tau, 1, rho_fn, u_fn, 1, cells, 0.1)
         lat.step(1)
-        check_sampled(lat, 2, dims, eq, 0, tau, 1, rho_fn, u_fn, 2, cells)
+        check_sampled(lat, 2, dims, eq, 0, tau, 1, rho_fn, u_fn, 2, cells, 0.1)
         lat.close()
 
 
@@ -183,8 +206,47 @@ def test_lattice_over_2_31_cells(shape):
     cells = sample_cells(dims, 32, seed=13)
     cells[-1] = (n - 1, n - 1, n - 1)  # the last cell: index n^3 - 1 > 2^31
     lat.step(1)
-    check_sampled(lat, 3, dims, core.EQ_ENTROPIC, 0, tau, 2, rho_fn, u_fn, 1, cells)
+    check_sampled(lat, 3, dims, core.EQ_ENTROPIC, 0, tau, 2, rho_fn, u_fn, 1, cells, u0)
     lat.step(1)
-    check_sampled(lat, 3, dims, core.EQ_ENTROPIC, 0, tau, 2, rho_fn, u_fn, 2, cells)
+    check_sampled(lat, 3, dims, core.EQ_ENTROPIC, 0, tau, 2, rho_fn, u_fn, 2, cells, u0)
     lat.close()
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec", [2, 1])
+def test_turbulence_1024x512x512_sampled(prec):
+    """The decaying-turbulence box at full size (1024 x 512 x 512, tau - 1/2 = 1e-4, the
+    random solenoidal field with E(k) ~ k^4 exp(-2 (k/8)^2), u_rms = 0.05) in the autotuned
+    launch shape: sampled cells after 1 and 2 steps against the oracle, which starts from
+    the same generated field values (gathered at each patch)."""
+    import torch
+    from paper_2303_08163_gb300 import lbm
+    dims = (1024, 512, 512)
+    nx, ny, _ = dims
+    tau = 0.5 + 1e-4
+    rho, u = inputs.random_solenoidal_torch(dims, u_rms=0.05, device="cuda")
+    umax = 1.1 * float(u.abs().max())  # of the input field, with room for two steps
+
+    def gather(t, ix, iy, iz):
+        flat = torch.from_numpy(np.ascontiguousarray(ix + nx * (iy + ny * iz), dtype=np.int64).reshape(-1))
+        return t[..., flat.to(t.device)].double().cpu().numpy()
+
+    def rho_fn(ix, iy, iz):
+        return gather(rho, ix, iy, iz).reshape(np.shape(ix))
+
+    def u_fn(ix, iy, iz):
+        return gather(u, ix, iy, iz).reshape((3,) + np.shape(ix))
+
+    lat = lbm.Lattice(lbm.D3Q27, dims, tau, lbm.ENTROPIC, 0, prec)
+    lat.init_fields(rho, u, dtype=np.float32)
+    lat.set_option(lbm.OPT_TUNE, 1)  # the benchmark's launch shape
+    assert lat.launch_info()["kernel"] == lbm.KERNEL_TMA
+    lat.init_fields(rho, u, dtype=np.float32)
+    cells = sample_cells(dims, 32, seed=29 + prec)
+    lat.step(1)
+    check_sampled(lat, 3, dims, core.EQ_ENTROPIC, 0, tau, prec, rho_fn, u_fn, 1, cells, umax)
+    lat.step(1)
+    check_sampled(lat, 3, dims, core.EQ_ENTROPIC, 0, tau, prec, rho_fn, u_fn, 2, cells, umax)
+    lat.close()
+    del rho, u
     torch.cuda.empty_cache()
