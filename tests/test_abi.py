@@ -85,3 +85,17 @@ def test_null_object_calls_fail_cleanly(lib):
     assert lib.lbm_sync(None) == lbm.EINVAL
     lib.lbm_destroy(None)
     lib.lbm_batch_destroy(None)
+
+
+def test_status_codes_match_the_header():
+    """Every enumerator of enum lbm_status in lbm.h has the same value in the binding."""
+    import re
+    from paper_2303_08163_gb300 import lbm
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    body = text[text.index("enum lbm_status"):]
+    body = body[:body.index("};")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    codes = {m.group(1): int(m.group(2)) for m in re.finditer(r"(LBM_[A-Z]+)\s*=\s*(-?\d+)", body)}
+    assert codes["LBM_ECHECK"] == lbm.ECHECK == -7
+    for name, value in codes.items():
+        assert lbm.STATUS_NAMES[value] == name
