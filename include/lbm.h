@@ -192,7 +192,8 @@ int lbm_launch_info(lbm_ctx *ctx, int64_t out[8]);
 /*
  * Choose the step kernel's launch shape explicitly.  shape = {kernel, threads, stages,
  * rows, seg, cap}: kernel 1 = generic (threads per block, the rest ignored), 2 = TMA
- * row-staged with `threads` colliding threads per block (a multiple of 32, at most 256;
+ * row-staged with `threads` colliding threads per block (a multiple of 32, at most 256,
+ * 512 for D2Q9 with binary16 storage;
  * one copy-issuing warp is added), `stages` shared-memory stages (2..8), `rows`
  * rows per job when whole rows fit, `seg` cells per row segment (seg >= Nx for whole
  * rows; otherwise a multiple of 16 / sizeof(storage)) and `cap` bytes per direction

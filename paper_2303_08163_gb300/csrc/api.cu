@@ -382,8 +382,11 @@ int autotune(lbm_ctx *c) {
             } else {
                 geo.push_back({1, (cap / es - 2 * U) / U * U});
             }
+            const std::vector<int> ths = tma_thread_limit(c->lat) > 256
+                                             ? std::vector<int>{128, 192, 256, 384, 512}
+                                             : std::vector<int>{128, 192, 256};
             for (auto rs : geo)
-                for (int th : {128, 192, 256})
+                for (int th : ths)
                     for (int st : {2, 3, 4, 6, 8}) {
                         TmaShape t{};
                         t.threads = th;

@@ -36,7 +36,9 @@
 namespace lbmd {
 
 using lbmh::kTmaMaxStages;
-constexpr int kTmaMaxThreads = 256;  // consumer threads; one producer warp more
+constexpr int kTmaMaxThreads = 256;  // consumer threads of the D3Q27 kernels; one producer warp more
+// D2Q9 binary16 kernels (under 100 registers) may run up to 512 consumers
+__host__ __device__ constexpr int tma_max_threads(int D, int P) { return D == 2 && P == 2 ? 512 : kTmaMaxThreads; }
 
 // bufstride (elements between direction buffers) equals the compile-time buffer
 // capacity CAPB / sizeof(storage) of the kernel instantiation.
@@ -411,7 +413,7 @@ __device__ __forceinline__ void tma_compute_pairs(const lbmh::StepArgs &a, const
 }
 
 template <int D, int P, int EQ, bool BULK, int CAPB>
-__global__ void __launch_bounds__(kTmaMaxThreads + 32) k_step_tma(const lbmh::StepArgs a, const TmaGeom g) {
+__global__ void __launch_bounds__(tma_max_threads(D, P) + 32) k_step_tma(const lbmh::StepArgs a, const TmaGeom g) {
     using T = typename Storage<P>::T;
     constexpr int Q = qof(D);
     extern __shared__ __align__(128) unsigned char smem_raw[];

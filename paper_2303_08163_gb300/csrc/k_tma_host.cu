@@ -58,6 +58,8 @@ static lbmd::TmaGeom geom(const Lattice &lat, const TmaShape &t) {
 // Dynamic shared memory of a shape, or -1 when the shape is invalid: the segment must be
 // a multiple of the 16-byte unit, the rows of a job must fit the direction buffer and
 // the stage count must be in [2, 8].
+int tma_thread_limit(const Lattice &lat) { return lbmd::tma_max_threads(lat.D, lat.P); }
+
 int tma_smem_bytes(const Lattice &lat, const TmaShape &t) {
     const int U = 16 / esize(lat.P);
     if (t.stages < 2 || t.stages > kTmaMaxStages) return -1;
@@ -66,7 +68,7 @@ int tma_smem_bytes(const Lattice &lat, const TmaShape &t) {
     const lbmd::TmaGeom g = geom(lat, t);
     if ((int64_t)g.rows * g.rowstride > g.bufstride) return -1;
     if (g.njobs >= ((int64_t)1 << 31)) return -1;
-    if (t.threads < 32 || t.threads > lbmd::kTmaMaxThreads || t.threads % 32) return -1;
+    if (t.threads < 32 || t.threads > lbmd::tma_max_threads(lat.D, lat.P) || t.threads % 32) return -1;
     const int64_t bytes = (int64_t)t.stages * lbmd::qof(lat.D) * t.cap;
     return bytes > 227 * 1024 ? -1 : (int)bytes;
 }

@@ -69,6 +69,8 @@ int diag_blocks_generic(int64_t ncell);
 // k_tma_*.cu
 bool tma_supported(const Lattice &lat);
 int tma_smem_bytes(const Lattice &lat, const TmaShape &t);
+// Largest number of colliding threads per block of the TMA kernel for the lattice.
+int tma_thread_limit(const Lattice &lat);
 cudaError_t tma_prepare(const Lattice &lat, int eq, int bulk, int cap, int smem_bytes);
 cudaError_t step_tma(const StepArgs &a, const TmaShape &t, cudaStream_t s);
 int tma_max_blocks_per_sm(const Lattice &lat, int eq, int bulk, const TmaShape &t);
