@@ -762,6 +762,10 @@ def run_batch(args, w, torch, lbm, dev, rank, ws):
     b.step(args.warmup)
     b.sync()
     stream = torch.cuda.current_stream()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(torch.cuda.current_device()) as clk:
         e0.record(stream)
@@ -769,15 +773,42 @@ def run_batch(args, w, torch, lbm, dev, rank, ws):
         e1.record(stream)
         e1.synchronize()
     ms = e0.elapsed_time(e1)
-    glups = total * args.steps / (ms * 1e-3) / 1e9
+    # end to end through the C ABI: pinned host fields in, all steps, moments out
+    rho_h = torch.from_numpy(rho).pin_memory()
+    u_h = torch.from_numpy(u).pin_memory()
+    rout = torch.empty(total, dtype=torch.float64).pin_memory()
+    uout = torch.empty(total * 2, dtype=torch.float64).pin_memory()
+    b.init_fields(rho_h, u_h)
+    b.moments(out=(rout, uout))  # untimed first round trip
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    b.init_fields(rho_h, u_h)
+    b.step(args.steps)
+    b.moments(out=(rout, uout))
+    f1.record(stream)
+    f1.synchronize()
+    e2e_ms = f0.elapsed_time(f1)
+    if ws > 1:
+        t = torch.tensor([ms, e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_ms = float(t[0]), float(t[1])
+        dist.barrier()
+    glups = aggregate(ws, total, args.steps, [ms])
+    e2e = {"value": aggregate(ws, total, args.steps, [e2e_ms]), "unit": "GLUPS",
+           "h2d_bytes_per_step": (rho_h.numel() + u_h.numel()) * 8 / args.steps,
+           "d2h_bytes_per_step": (rout.numel() + uout.numel()) * 8 / args.steps,
+           "path": "lbm_batch_init_fields(host) + lbm_batch_step(K) + lbm_batch_moments(host), pinned buffers"}
+    if rank != 0:
+        return
     # FP64 collisions: the roofline is the FP64 pipe.  Peak = 152 SMs x 2 FP64 FMA per
     # cycle x 2 flops x the median SM clock under load
     fpc = fp64_flops_per_cell(w["eq"], args.bulk)
     clocks = clk.summary()
     sm_ghz = (clocks.get("sm_mhz") or 2070.0) / 1e3
     fp64_peak = 152 * 2 * 2 * sm_ghz  # GFLOP/s
-    achieved = fpc * glups  # GFLOP/s
-    hbm = 2 * 9 * 8 * glups
+    achieved = fpc * glups / ws  # GFLOP/s of one GPU
+    hbm = 2 * 9 * 8 * glups / ws  # GB/s of one GPU
     g, desc = oracle_sample(w, args.cpu_seconds)
     line = {"metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -791,7 +822,7 @@ def run_batch(args, w, torch, lbm, dev, rank, ws):
                          "flops_per_cell_update": fpc,
                          "hbm_GB_s": hbm, "hbm_frac": hbm / (measured_peaks().get("hbm_gbs") or 6800.0)},
             "cpu_baseline": {"value": g, "unit": "GLUPS", "cores": 1, "kind": "oracle", "sample": desc},
-            "gpu_launches": 1, "clocks": clocks}
+            "e2e": e2e, "gpu_launches": 1, "clocks": clocks}
     print(json.dumps(line), flush=True)
 
 

@@ -329,7 +329,14 @@ class Batch:
         _check(load().lbm_batch_status(self._h, s.ctypes.data_as(_pi32)))
         return s
 
-    def moments(self, dtype=np.float64):
+    def moments(self, dtype=np.float64, out=None):
+        """rho (total,) and u (per instance [D][cells], packed) as NumPy arrays, or into
+        the torch tensors `out` (host or device)."""
+        if out is not None:
+            rho, u = out
+            _check(load().lbm_batch_moments(self._h, ctypes.c_void_p(rho.data_ptr()),
+                                            ctypes.c_void_p(u.data_ptr()), _dt(dtype), int(rho.is_cuda)))
+            return rho, u
         total = int(self.cell_start[-1])
         rho = np.empty(total, dtype=dtype)
         u = np.empty(total * self.D, dtype=dtype)
