@@ -380,7 +380,13 @@ int autotune(lbm_ctx *c) {
                 geo.push_back({rmax, (int)c->lat.nx});
                 if (rmax > 1) geo.push_back({std::max(1, rmax / 2), (int)c->lat.nx});
             } else {
-                geo.push_back({1, (cap / es - 2 * U) / U * U});
+                // the longest segment the buffer holds, and the same number of segments
+                // made equal (no short ragged last segment with a job's full overhead)
+                const int smax = (cap / es - 2 * U) / U * U;
+                geo.push_back({1, smax});
+                const int64_t nseg = (c->lat.nx + smax - 1) / smax;
+                const int sbal = (int)(((c->lat.nx + nseg - 1) / nseg + U - 1) / U * U);
+                if (sbal < smax) geo.push_back({1, sbal});
             }
             const std::vector<int> ths = tma_thread_limit(c->lat) > 256
                                              ? std::vector<int>{128, 192, 256, 384, 512}
