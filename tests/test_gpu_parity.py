@@ -390,3 +390,50 @@ def test_batch_d3q27_parity_and_probes():
             ncell = int(c1 - c0)
             assert np.all(np.abs(series[k] - sk) <= 1e-12 * np.abs(sk) + 1e-13 * ncell)
         b.close()
+
+
+# ------------------------------------------------------------------- degenerate states
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("shape", [(1, 128), (2, 128, 2, 2, 16, 1024)])
+def test_rest_state_is_a_fixed_point(prec, shape):
+    """rho = rho0, u = 0: every shifted population is exactly 0, and the collision and the
+    streaming keep it exactly 0 (a fixed point of the scheme, in every precision and
+    kernel path, with the bulk correction on)."""
+    lbm = lbm_mod()
+    dims = (16, 6, 4)
+    lat = lbm.Lattice(lbm.D3Q27, dims, 0.56, lbm.ENTROPIC, 1, prec)
+    lat.set_launch_shape(*shape)
+    n = int(np.prod(dims))
+    lat.init_fields(np.ones(n), np.zeros((3, n)))
+    lat.step(5)
+    raw = lat.get_populations("storage")
+    assert np.all(raw == 0)
+    lat.close()
+
+
+@pytest.mark.parametrize("eq,u0", [(core.EQ_ENTROPIC, (0.9, -0.6, 0.3)), (core.EQ_POLY2, (0.3, -0.2, 0.1)),
+                                   (core.EQ_PRODUCT, (0.4, 0.3, -0.2))])
+def test_uniform_flow_is_a_fixed_point(eq, u0):
+    """A uniform flow f = f^eq(rho, U) streams onto itself and collides to itself, so it
+    is invariant; at |U| up to 0.9 per axis for the entropic equilibrium (close to its
+    limit |u| < 1) the GPU FP64 state stays at the oracle's over 7 steps.  Tolerance:
+    1e-12 relative, plus an absolute 1e-14 w_i, because the GPU stores f - w rho0 and at
+    this speed some f_i are ~1e-4 of w_i, so the rounding of the stored value (2^-53 of
+    about w_i per step) is no longer small against f_i itself."""
+    lbm = lbm_mod()
+    dims = (8, 5, 3)
+    n = int(np.prod(dims))
+    rho = np.full(n, 1.05)
+    u = np.tile(np.array(u0)[:, None], (1, n))
+    lat = lbm.Lattice(lbm.D3Q27, dims, 0.53, eq, 1, lbm.F64)
+    lat.init_fields(rho, u)
+    lat.step(7)
+    got = lat.get_populations()
+    f0 = core.init(3, dims, eq, rho, u)
+    ref = core.step(3, dims, eq, 1, 0.53, 7, f0)
+    _, w = core.lattice(3)
+    tol = 1e-12 * np.abs(ref) + 1e-14 * w[:, None]
+    assert np.all(np.abs(got - ref) <= tol)
+    assert np.all(np.abs(got - f0) <= tol)
+    lat.close()
