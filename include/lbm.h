@@ -193,9 +193,9 @@ int lbm_launch_info(lbm_ctx *ctx, int64_t out[8]);
  * Choose the step kernel's launch shape explicitly.  shape = {kernel, threads, stages,
  * rows, seg, cap}: kernel 1 = generic (threads per block, the rest ignored), 2 = TMA
  * row-staged with `threads` colliding threads per block (a multiple of 32, at most 256,
- * 512 for D2Q9 with binary16 storage;
- * one copy-issuing warp is added), `stages` shared-memory stages (2..8), `rows`
- * rows per job when whole rows fit, `seg` cells per row segment (seg >= Nx for whole
+ * 512 for D2Q9 with binary16 storage; one copy-issuing warp is added), `stages`
+ * shared-memory stages (2..8), `rows` rows per job when whole rows fit, `seg` cells per
+ * row segment (seg >= Nx for whole
  * rows; otherwise a multiple of 16 / sizeof(storage)) and `cap` bytes per direction
  * buffer (1024, 2048, 4096 or 8192).  The block count is the largest that fits on the
  * device.  Returns LBM_EINVAL for a shape the lattice or the device cannot run.
