@@ -48,6 +48,7 @@ def _load():
             "oracle_diagnostics": (ci, [ci, lp, dp, dp]),
             "oracle_probe": (ci, [ci, lp, dp, ip, dp]),
             "oracle_run_probed": (ci, [ci, lp, ci, ci, cd, i64, i64, ip, dp, dp, dp]),
+            "oracle_set_threads": (ci, [ci]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -119,6 +120,13 @@ def init(D, dims, eq_kind, rho, u):
     f = np.zeros((3 ** D, n))
     _check(_load().oracle_init(int(D), _lp(d), int(eq_kind), _dp(rho), _dp(uu), _dp(f)), "init")
     return f
+
+
+def set_threads(n):
+    """Host threads used by `step` from now on (1 by default); returns the number the
+    library will use (1 when it was built without OpenMP).  Every thread count gives the
+    same result bit for bit."""
+    return _load().oracle_set_threads(int(n))
 
 
 def step(D, dims, eq_kind, bulk_corr, tau, n, f):

@@ -248,6 +248,25 @@ int oracle_init(int D, const int64_t *dims, int eq_kind, const double *rho, cons
 }
 
 /*
+ * Host threads of oracle_step (1 by default).  The cells of one step are independent:
+ * each reads the state f and writes its post-collision values to distinct slots of g,
+ * so the rows of the lattice are shared out between threads without changing any
+ * cell's arithmetic; the result is the same bit for bit for every thread count.  Builds
+ * without OpenMP run one thread whatever is asked.
+ */
+static int or_threads = 1;
+
+int oracle_set_threads(int n)
+{
+    or_threads = n < 1 ? 1 : n;
+#ifdef _OPENMP
+    return or_threads;
+#else
+    return 1;
+#endif
+}
+
+/*
  * n time steps of Eq. (1) on two arrays: for each cell compute rho and u from the
  * populations, the equilibrium, the collision frequency, the post-collision value
  * f_i + 2 beta (f_i^eq - f_i), and write it to cell r + c_i (periodic).  f holds the
@@ -258,30 +277,35 @@ int oracle_step(int D, const int64_t *dims, int eq_kind, int bulk_corr, double t
 {
     or_lattice L;
     int64_t nx = dims[0], ny = dims[1], nz = dims[2];
-    int64_t ncell = nx * ny * nz, s;
-    double feq[27];
+    int64_t ncell = nx * ny * nz, nrow = ny * nz, s;
     if (D < 1 || D > 3) return -1;
+    if (eq_kind != OR_EQ_ENTROPIC && eq_kind != OR_EQ_POLY2 && eq_kind != OR_EQ_PRODUCT) return -1;
     or_make_lattice(D, &L);
     for (s = 0; s < n; ++s) {
-        int64_t x, y, z;
-        for (z = 0; z < nz; ++z)
-            for (y = 0; y < ny; ++y)
-                for (x = 0; x < nx; ++x) {
-                    int64_t idx = x + nx * (y + ny * z);
-                    double rho, u[3], om;
-                    int i;
-                    or_moments_cell(&L, f, ncell, idx, &rho, u);
-                    if (or_feq(&L, eq_kind, rho, u, feq)) return -1;
-                    om = oracle_omega(D, eq_kind, bulk_corr, tau, u);
-                    for (i = 0; i < L.Q; ++i) {
-                        double fi = f[(int64_t)i * ncell + idx];
-                        double post = fi + om * (feq[i] - fi);
-                        int64_t xd = or_wrap(x + L.c[i][0], nx);
-                        int64_t yd = or_wrap(y + L.c[i][1], ny);
-                        int64_t zd = or_wrap(z + L.c[i][2], nz);
-                        g[(int64_t)i * ncell + xd + nx * (yd + ny * zd)] = post;
-                    }
+        int64_t row;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(or_threads)
+#endif
+        for (row = 0; row < nrow; ++row) {
+            int64_t y = row % ny, z = row / ny, x;
+            double feq[27];
+            for (x = 0; x < nx; ++x) {
+                int64_t idx = x + nx * (y + ny * z);
+                double rho, u[3], om;
+                int i;
+                or_moments_cell(&L, f, ncell, idx, &rho, u);
+                or_feq(&L, eq_kind, rho, u, feq);
+                om = oracle_omega(D, eq_kind, bulk_corr, tau, u);
+                for (i = 0; i < L.Q; ++i) {
+                    double fi = f[(int64_t)i * ncell + idx];
+                    double post = fi + om * (feq[i] - fi);
+                    int64_t xd = or_wrap(x + L.c[i][0], nx);
+                    int64_t yd = or_wrap(y + L.c[i][1], ny);
+                    int64_t zd = or_wrap(z + L.c[i][2], nz);
+                    g[(int64_t)i * ncell + xd + nx * (yd + ny * zd)] = post;
                 }
+            }
+        }
         memcpy(f, g, sizeof(double) * (size_t)(ncell * L.Q));
     }
     return 0;

@@ -450,3 +450,21 @@ def test_product_form_diagonal_limit():
     kgrid = np.linspace(0.0, math.pi, 13)
     assert analysis.growth_max(2, core.EQ_PRODUCT, tau, lim - 0.02, math.pi / 4, kgrid) <= 1 + 1e-12
     assert analysis.growth_max(2, core.EQ_PRODUCT, tau, lim + 0.03, math.pi / 4, kgrid) > 1 + 1e-6
+
+
+@pytest.mark.parametrize("D,dims", [(2, (23, 17, 1)), (3, (9, 7, 5))])
+@pytest.mark.parametrize("eq", [core.EQ_ENTROPIC, core.EQ_POLY2, core.EQ_PRODUCT])
+def test_threaded_step_is_bitwise_single_thread(D, dims, eq):
+    """The all-core oracle (rows of the lattice shared out between host threads) computes
+    every cell exactly as the single-thread oracle does: the states agree bit for bit."""
+    rho, u = inputs.random_state(D, dims, seed=61 + eq, u_max=0.15)
+    f0 = core.init(D, dims, eq, rho, u)
+    core.set_threads(1)
+    one = core.step(D, dims, eq, 1, 0.57, 6, f0)
+    used = core.set_threads(4)
+    try:
+        many = core.step(D, dims, eq, 1, 0.57, 6, f0)
+    finally:
+        core.set_threads(1)
+    assert used in (1, 4)
+    assert np.array_equal(one.view(np.uint64), many.view(np.uint64))
