@@ -41,7 +41,12 @@
  * Errors: every int-returning call returns LBM_OK (0) or a negative status code.  The
  *   message of the last failure on the calling thread is returned by lbm_last_error().
  *   LBM_ECUDA, LBM_ETIMEOUT and LBM_ENOMEM are sticky: the object refuses further work
- *   (LBM_ESTATE) until destroyed.
+ *   (LBM_ESTATE) until destroyed.  A step kernel whose bounded wait ran out records
+ *   LBM_ETIMEOUT in the object's device status word; every call that synchronises (lbm_sync,
+ *   lbm_diagnostics, lbm_diag_history, lbm_step with diagnostics, and the calls that return
+ *   data in host memory) reads that word and returns the error.  Calls that only enqueue
+ *   work (lbm_step without diagnostics, device-memory outputs) do not synchronise, so the
+ *   error surfaces at the next synchronising call.
  * Threads: an object may be used by one host thread at a time.
  */
 #ifndef LBM_H
@@ -126,7 +131,18 @@ typedef struct {
 int lbm_create(lbm_ctx **out, int lattice, const int64_t dims[3], double tau, int eq_kind,
                int bulk_corr, int precision, double rho0, void *cuda_stream);
 
-/* Set an lbm_option.  LBM_OPT_TUNE runs steps on the current state and then restores it. */
+/*
+ * Set an lbm_option.  LBM_OPT_TUNE times every candidate launch shape on a proxy lattice
+ * with the same row geometry (the same Nx, and Ny for D3Q27) and at most 2 GiB of
+ * populations in whole z-planes (y-rows for D2Q9), filled from the current state's first
+ * planes; the context's own state is not touched.  It keeps the fastest shape (among
+ * shapes within 0.5 % of it, the one with the least shared memory, then the fewest stages
+ * and threads), remembers it for lattices of the same kind and size (and in the file named
+ * by the environment variable LBM_TUNE_CACHE, if set; a remembered shape is checked
+ * against the lattice and the device before it is used).  A candidate whose bounded wait
+ * ran out is discarded.  Returns LBM_ENOMEM, with the context still usable, if the proxy
+ * cannot be allocated.
+ */
 int lbm_set_option(lbm_ctx *ctx, int option, int64_t value);
 
 /*
@@ -195,10 +211,11 @@ int lbm_launch_info(lbm_ctx *ctx, int64_t out[8]);
  * row-staged with `threads` colliding threads per block (a multiple of 32, at most 256,
  * 512 for D2Q9 with binary16 storage; one copy-issuing warp is added), `stages`
  * shared-memory stages (2..8), `rows` rows per job when whole rows fit, `seg` cells per
- * row segment (seg >= Nx for whole
- * rows; otherwise a multiple of 16 / sizeof(storage)) and `cap` bytes per direction
- * buffer (1024, 2048, 4096 or 8192).  The block count is the largest that fits on the
- * device.  Returns LBM_EINVAL for a shape the lattice or the device cannot run.
+ * row segment (seg >= Nx for whole rows; otherwise a multiple of 16 / sizeof(storage), and
+ * never below it) and `cap` bytes per direction buffer (1024, 2048, 4096 or 8192).  The
+ * one-cell kernel takes at most 256 threads.  The block count is the largest that fits on
+ * the device.  Returns LBM_EINVAL for a negative entry, an entry above INT32_MAX, or a
+ * shape the lattice or the device cannot run.
  */
 int lbm_set_launch_shape(lbm_ctx *ctx, const int64_t shape[6]);
 
@@ -263,6 +280,27 @@ int lbm_batch_info(lbm_batch *b, int64_t *total_cells, int64_t *step);
 /* Launch shape of the batched kernel: out[0] = threads per block, out[1] = blocks,
  * out[2] = largest per-block cell load, out[3] = mean per-block cell load. */
 int lbm_batch_launch_info(lbm_batch *b, int64_t out[4]);
+
+/*
+ * Choose the batched kernel's launch shape: `threads` per block (a multiple of 32 in
+ * [32, 256]) and `blocks` (1 .. min(count, 32 x the SM count)).  Instances are
+ * re-assigned to the blocks longest-first (each to the least-loaded block so far); a
+ * block owns whole instances, so blocks never wait for one another and more blocks than
+ * fit on the GPU at once simply run in waves.  Returns LBM_EINVAL for other values.
+ */
+int lbm_batch_set_launch_shape(lbm_batch *b, int threads, int64_t blocks);
+
+/*
+ * Launch-shape autotuner of the batched kernel: times `steps` steps (1 .. 100000) of the
+ * current state under each candidate shape (64, 128 or 256 threads; 1, 2, 3, 4, 6, 8, 12
+ * or 16 blocks per SM), twice, and keeps the fastest (among shapes within 0.5 % of it, the
+ * one with the fewest blocks, then threads).  The state, the step counter and the status
+ * are restored afterwards, so the call changes only the launch shape; the probes of the
+ * timed steps are written to samples that the next lbm_batch_step rewrites.  Needs one
+ * temporary copy of the state (Q x total cells doubles): LBM_ENOMEM, with the object
+ * still usable, if it cannot be allocated.  Synchronises.
+ */
+int lbm_batch_autotune(lbm_batch *b, int64_t steps);
 
 int lbm_batch_sync(lbm_batch *b);
 void lbm_batch_destroy(lbm_batch *b);

@@ -94,8 +94,12 @@ extern "C" int lbm_diagnostics_noalloc(int lattice, const int64_t dims[3], const
     if (!dims || !f || !out) return noalloc_fail(LBM_EINVAL, "null argument");
     if (lattice != LBM_D2Q9 && lattice != LBM_D3Q27) return noalloc_fail(LBM_EINVAL, "bad lattice");
     for (int a = 0; a < 3; ++a)
-        if (dims[a] < 1) return noalloc_fail(LBM_EINVAL, "dims must be >= 1");
+        if (dims[a] < 1 || dims[a] > (1 << 30)) return noalloc_fail(LBM_EINVAL, "dims must be in [1, 2^30]");
     if (lattice == LBM_D2Q9 && dims[2] != 1) return noalloc_fail(LBM_EINVAL, "D2Q9 needs dims[2] == 1");
+    // the same size limits as lbm_create: no int64 overflow of the cell count, at most 2^40 cells
+    const int64_t xy = dims[0] * dims[1];
+    if (xy / dims[0] != dims[1] || dims[2] > (((int64_t)1 << 40) / xy))
+        return noalloc_fail(LBM_EINVAL, "lattice too large (more than 2^40 cells)");
     if (blocks < 1 || blocks > kNoAllocMaxBlocks)
         return noalloc_fail(LBM_EINVAL,
                             "blocks must be in [1, 1024]: the static scratch holds 1024 partial sums");

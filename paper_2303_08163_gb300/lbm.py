@@ -67,6 +67,8 @@ SIGNATURES = {
     "lbm_batch_get_populations": (_i, [_vp, _vp, _i, _i]),
     "lbm_batch_info": (_i, [_vp, _p64, _p64]),
     "lbm_batch_launch_info": (_i, [_vp, _p64]),
+    "lbm_batch_set_launch_shape": (_i, [_vp, _i, _i64]),
+    "lbm_batch_autotune": (_i, [_vp, _i64]),
     "lbm_batch_sync": (_i, [_vp]),
     "lbm_batch_destroy": (None, [_vp]),
     "lbm_last_error": (ctypes.c_char_p, []),
@@ -216,9 +218,19 @@ class Lattice:
         _check(load().lbm_diag_history(self._h, arr, int(max_records), ctypes.byref(cnt)))
         return [_diag_dict(arr[i]) for i in range(min(cnt.value, max_records))]
 
-    def get_populations(self, dtype=np.float64):
+    def get_populations(self, dtype=np.float64, out=None):
         """Canonical populations (Q, ncell); dtype="storage" returns the stored shifted
-        values f - w rho0 in the storage type, bit for bit."""
+        values f - w rho0 in the storage type, bit for bit.  With `out` (a contiguous torch
+        tensor of Q * ncell elements on the lattice's device, of the storage type's size for
+        "storage"), the populations are written there without a host copy."""
+        if out is not None:
+            dt = DT_STORAGE if isinstance(dtype, str) and dtype == "storage" else _dt(dtype)
+            want = {DT_STORAGE: np.dtype(STORAGE_NUMPY[self.precision]).itemsize, DT_F64: 8, DT_F32: 4}[dt]
+            if (not out.is_cuda or not out.is_contiguous() or out.element_size() != want
+                    or out.numel() != self.Q * self.ncell):
+                raise ValueError("out must be a contiguous device tensor of Q * ncell elements of the requested type")
+            _check(load().lbm_get_populations(self._h, ctypes.c_void_p(out.data_ptr()), dt, 1))
+            return out
         if isinstance(dtype, str) and dtype == "storage":
             f = np.empty((self.Q, self.ncell), dtype=STORAGE_NUMPY[self.precision])
             _check(load().lbm_get_populations(self._h, ctypes.c_void_p(f.ctypes.data), DT_STORAGE, 0))
@@ -359,6 +371,13 @@ class Batch:
         out = (ctypes.c_int64 * 4)()
         _check(load().lbm_batch_launch_info(self._h, out))
         return dict(zip(["threads", "blocks", "max_load", "mean_load"], list(out)))
+
+    def set_launch_shape(self, threads, blocks):
+        _check(load().lbm_batch_set_launch_shape(self._h, int(threads), int(blocks)))
+
+    def autotune(self, steps=10):
+        """lbm_batch_autotune: keep the fastest launch shape (the state is unchanged)."""
+        _check(load().lbm_batch_autotune(self._h, int(steps)))
 
     def sync(self):
         _check(load().lbm_batch_sync(self._h))
