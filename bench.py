@@ -40,23 +40,40 @@ if ROOT not in sys.path:
 METRIC = "GLUPS and % of HBM roofline; FP16-store vs FP32/FP64 at stated L2 velocity error"
 
 
-def fp64_flops_per_cell(eq, bulk):
-    """Algorithmic FP64 flops of one D2Q9 collision as the kernels write it (an FMA is two
-    flops, a division or a square root one).  Entropic: the moment sums 15, rho^2 1, per
-    axis 3j, T = sqrt(rho^2 + 3j^2) and q = rho + T (2 x 5), the one division of
-    rho q_x q_y with its products (4), per axis u, S - 1, 3u, d(+1), d(-1) (2 x 9), drho 1,
-    the rate terms 10 (1 - 2beta and, per weight class, 2beta w, 2beta w rho, 2beta w drho),
-    t = 1 + d 3, per direction h and the relaxation 9 x 6.  Quadratic: moments 18 (the sums,
-    1/rho, two products), drho 1, rate terms 10, u^2 3, -3/2 u^2 1, the diagonal sums 2,
-    9 x 8.  Product form: moments 18, drho 1, rate terms 10, per-axis factors 2 x 7,
-    t = 1 + d 3, 9 x 6.  The bulk correction adds the rate formula (6 entropic, 5
-    otherwise)."""
+def fp64_flops_per_cell(eq, bulk, D=2):
+    """Algorithmic FP64 flops of one collision as the kernels write it (an FMA is two
+    flops, a division or a square root one, a negation or a max none).
+    D2Q9 entropic: the moment sums 15, rho^2 1, per axis 3j, T = sqrt(rho^2 + 3j^2) and
+    q = rho + T (2 x 5), the one division of rho q_x q_y with its products (4), per axis u,
+    S - 1, 3u, d(+1), d(-1) (2 x 9), drho 1, the rate terms 10 (1 - 2beta and, per weight
+    class, 2beta w, 2beta w rho, 2beta w drho), t = 1 + d 3, per direction h and the
+    relaxation 9 x 6.  Quadratic: moments 18 (the sums, 1/rho, two products), drho 1, rate
+    terms 10, u^2 3, -3/2 u^2 1, the diagonal sums 2, 9 x 8.  Product form: moments 18,
+    drho 1, rate terms 10, per-axis factors 2 x 7, t = 1 + d 3, 9 x 6.
+    D3Q27 (the same conventions): moment sums 50; entropic: rho^2 1, per axis 3 x 5, the
+    division with its products 7, per axis 3 x 9, drho 1, rate terms 13 (four weight
+    classes), t = 1 + d 6, per (c_x, c_y) pair the partial products 9 x 3, per direction
+    27 x 6.  Product form: moments 54, drho 1, rate terms 13, per-axis factors 3 x 7,
+    t = 1 + d 6, 9 x 3, 27 x 6.  Quadratic: moments 54, drho 1, rate terms 13, u^2 5,
+    -3/2 u^2 1, diagonal sums 2, 27 x 8 plus 18 c_z additions.  The bulk correction adds
+    the rate formula (6 entropic, 5 otherwise)."""
+    if D == 2:
+        if eq == 0:
+            return 15 + 1 + 10 + 4 + 18 + 1 + 10 + 3 + 54 + (6 if bulk else 0)
+        base = 18 + 1 + 10
+        if eq == 1:
+            return base + 3 + 1 + 2 + 72 + (5 if bulk else 0)
+        return base + 14 + 3 + 54 + (5 if bulk else 0)
     if eq == 0:
-        return 15 + 1 + 10 + 4 + 18 + 1 + 10 + 3 + 54 + (6 if bulk else 0)
-    base = 18 + 1 + 10
+        return 50 + 1 + 15 + 7 + 27 + 1 + 13 + 6 + 27 + 162 + (6 if bulk else 0)
     if eq == 1:
-        return base + 3 + 1 + 2 + 72 + (5 if bulk else 0)
-    return base + 14 + 3 + 54 + (5 if bulk else 0)
+        return 54 + 1 + 13 + 5 + 1 + 2 + 27 * 8 + 18 + (5 if bulk else 0)
+    return 54 + 1 + 13 + 21 + 6 + 27 + 162 + (5 if bulk else 0)
+
+
+def fp64_peak_gflops(sm_mhz):
+    """FP64 peak of the GPU: 152 SMs x 2 FP64 FMA per cycle x 2 flops x the SM clock."""
+    return 152 * 2 * 2 * (sm_mhz or 2070.0) / 1e3
 
 
 PREC = {"f64": 0, "f32": 1, "f16s": 2}
@@ -77,14 +94,17 @@ def parse():
     p.add_argument("--n", type=int, default=None, help="lattice side (default: the workload's)")
     p.add_argument("--diag-every", type=int, default=10)
     p.add_argument("--no-extras", action="store_true", help="skip the comparison runs")
-    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--cpu-seconds", type=float, default=3.0,
+                   help="length of each of the 3 timed oracle runs of the CPU baseline")
+    p.add_argument("--batch-count", type=int, default=4096, help="instances of the batch workload")
     p.add_argument("--accuracy", action="store_true",
                    help="only run the long accuracy checks of the workload (Taylor-Green: FP32 and "
                         "binary16 against FP64; shear layer: divergence step) and print them")
     p.add_argument("--long-steps", type=int, default=None,
                    help="steps of the long accuracy runs (Taylor-Green 20000, shear layer 10000)")
     p.add_argument("--shape", default=None,
-                   help="fixed launch shape kernel,threads,stages,rows,seg,cap (no tuning)")
+                   help="fixed launch shape (no tuning): kernel,threads,stages,rows,seg,cap; "
+                        "for the batch workload threads,blocks")
     p.add_argument("--no-tune", action="store_true",
                    help="keep the default (or cached) launch shape instead of autotuning")
     return p.parse_args()
@@ -118,7 +138,7 @@ def workload(args):
         prec = PREC[args.precision or "f64"]
         return dict(name=f"D2Q9 {n}^2 periodic Taylor-Green vortex (u0=0.05, tau=0.8)",
                     D=2, dims=(n, n, 1), tau=0.8, prec=prec, eq=eq, u0=0.05)
-    return dict(name="4096 independent D2Q9 periodic lattices, sides log-uniform in [16,256], "
+    return dict(name=f"{args.batch_count} independent D2Q9 periodic lattices, sides log-uniform in [16,256], "
                      "one shear or acoustic wave each (amplitude 1e-4), FP64",
                 D=2, dims=None, tau=None, prec=0, eq=eq, u0=0.3)
 
@@ -212,18 +232,34 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, workload_name, ncell):
-    """DRAM bytes per launch from the committed ncu summary, scaled to ncell; None when the
-    kernel source changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+LAUNCH_KEYS = ("threads", "blocks", "stages", "rows", "seg", "smem_bytes")
+
+
+def traffic_records():
     try:
-        recs = json.load(open(path))
+        return json.load(open(os.path.join(ROOT, "profiles", "ncu_traffic.json")))
     except (OSError, ValueError):
-        return None
-    for r in recs:
-        if r.get("kernel") == kernel and r.get("workload") == workload_name and r.get("source_hash") == source_hash():
-            return r["dram_bytes_per_cell"] * ncell
-    return None
+        return []
+
+
+def ncu_traffic(kernel, workload_name, units, launch=None):
+    """DRAM bytes per launch from the committed ncu records, scaled to `units` (cells, or
+    cell updates for the batch) and the reason when there is none.  A record counts only
+    for the kernel source it was taken on (the step-kernel source hash) and, for the
+    single-lattice kernels, for the exact launch shape that ran (threads, blocks, stages,
+    rows, segment, shared memory): another shape moves other bytes."""
+    recs = [r for r in traffic_records() if r.get("kernel") == kernel and r.get("workload") == workload_name]
+    if not recs:
+        return None, "no ncu record for this kernel and workload"
+    recs = [r for r in recs if r.get("source_hash") == source_hash()]
+    if not recs:
+        return None, "the kernel source changed since the ncu records were taken"
+    if launch is not None:
+        recs = [r for r in recs if all(r.get("launch", {}).get(k) == launch.get(k) for k in LAUNCH_KEYS)]
+        if not recs:
+            shape = {k: launch.get(k) for k in LAUNCH_KEYS}
+            return None, f"no ncu record for the launch shape that ran {shape}"
+    return recs[0]["dram_bytes_per_cell"] * units, recs[0].get("captured_on")
 
 
 def aggregate(world, cells_per_rank, steps, rank_ms):
@@ -239,71 +275,132 @@ def dist_env():
 
 # ----------------------------------------------------------------------- CPU baseline leg
 
-def oracle_sample(w, seconds):
-    """Time the FP64 CPU oracle (single thread, as it stands) on a bounded sample of the
-    workload; returns (GLUPS, description)."""
-    from oracle import core
+def cpu_info():
+    """Model name and core counts of the host (reported beside the oracle timings)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except AttributeError:
+        usable = os.cpu_count()
+    import platform
+    return {"model": model or platform.machine(), "logical_cpus": os.cpu_count(), "usable_cpus": usable}
+
+
+def cpu_sample(w):
+    """The bounded sample of the workload the CPU oracle is timed on: (D, dims, eq, tau,
+    rho, u, description).  Taylor-Green: the same vortex at 128^3; turbulence: the same
+    spectrum on a 128 x 64 x 64 box; shear layer: the same layer at 1024^2; the small
+    Taylor-Green configuration: itself; the batch: the 64^2 instance table's first
+    instance kind at 256^2 (one shear wave on U0 = 0.1)."""
     from paper_2303_08163_gb300 import inputs
-    D = w["D"]
+    D, eq = w["D"], w["eq"]
     if w["dims"] is None:
-        n = 64
-        dims = (n, n, 1)
-        table = {"nx": [n], "ny": [n], "nmode": [2], "U0": [0.1], "tau": [0.8], "kind": [1], "amp": 1e-4}
+        dims = (256, 256, 1)
+        table = {"nx": [256], "ny": [256], "nmode": [2], "U0": [0.1], "tau": [0.8], "kind": [0], "amp": 1e-4}
         rho, u = inputs.linear_mode_fields(table, 0)
-        tau = 0.8
-    elif D == 3:
-        n = 48
-        dims = (n, n, n)
+        return D, dims, eq, 0.8, rho, u, "a D2Q9 256^2 lattice with one shear wave (amplitude 1e-4) on U0 = 0.1"
+    if "turbulence" in w["name"]:
+        dims = (128, 64, 64)
+        rho, u = inputs.random_solenoidal(dims, u_rms=0.05)
+        return D, dims, eq, w["tau"], rho, u, "the turbulence spectrum on a 128 x 64 x 64 box"
+    if D == 3:
+        n = 128
         rho, u = inputs.taylor_green_3d(n, u0=w["u0"])
-        tau = w["tau"]
-    else:
-        n = 256
-        dims = (n, n, 1)
-        rho, u = inputs.taylor_green_2d(n, u0=0.05)
-        tau = w["tau"]
-    f = core.init(D, dims, w["eq"], rho, u)
-    t0 = time.perf_counter()
-    f = core.step(D, dims, w["eq"], 0, tau, 1, f)
-    one = time.perf_counter() - t0
-    steps = max(1, int(seconds / max(one, 1e-6)))
-    t0 = time.perf_counter()
-    core.step(D, dims, w["eq"], 0, tau, steps, f)
-    dt = time.perf_counter() - t0
-    ncell = int(np.prod(dims))
-    return ncell * steps / dt / 1e9, (f"FP64 CPU oracle, single thread, D{D}Q{3 ** D} "
-                                      f"{'x'.join(str(d) for d in dims if d > 1)} sample of the workload, "
-                                      f"{steps} steps in {dt:.1f} s")
+        return D, (n, n, n), eq, w["tau"], rho, u, "the Taylor-Green vortex at 128^3 (same u0 and tau)"
+    if "shear" in w["name"]:
+        n = 1024
+        rho, u = inputs.double_shear_layer(n)
+        return D, (n, n, 1), eq, w["tau"], rho, u, "the double shear layer at 1024^2 (same tau)"
+    n = w["dims"][0]
+    rho, u = inputs.taylor_green_2d(n, u0=w["u0"])
+    return D, (n, n, 1), eq, w["tau"], rho, u, f"the whole {n}^2 Taylor-Green workload"
+
+
+def time_oracle(D, dims, eq, bulk, tau, f, threads, seconds, reps=3):
+    """Median over `reps` runs of the oracle's GLUPS on state f with `threads` host
+    threads, each run a whole number of steps of about `seconds`; returns (GLUPS, steps)."""
+    from oracle import core
+    used = core.set_threads(threads)
+    try:
+        t0 = time.perf_counter()
+        core.step(D, dims, eq, bulk, tau, 1, f)
+        one = time.perf_counter() - t0
+        steps = max(1, int(round(seconds / max(one, 1e-6))))
+        rates = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            core.step(D, dims, eq, bulk, tau, steps, f)
+            rates.append(int(np.prod(dims)) * steps / (time.perf_counter() - t0) / 1e9)
+    finally:
+        core.set_threads(1)
+    return statistics.median(rates), steps, used
+
+
+def oracle_baseline(w, bulk, seconds=4.0):
+    """The FP64 CPU oracle as it stands, timed on the host cores on a bounded sample of the
+    workload: all cores (OpenMP over the rows of the lattice; the cells and their
+    arithmetic are the same as with one thread, bit for bit) and a single thread, each the
+    median of 3 runs of about `seconds`."""
+    from oracle import core
+    D, dims, eq, tau, rho, u, what = cpu_sample(w)
+    f = core.init(D, dims, eq, rho, u)
+    info = cpu_info()
+    g_all, n_all, used = time_oracle(D, dims, eq, bulk, tau, f, info["usable_cpus"] or 1, seconds)
+    g_one, n_one, _ = time_oracle(D, dims, eq, bulk, tau, f, 1, seconds)
+    lat = f"D{D}Q{3 ** D} {'x'.join(str(d) for d in dims if d > 1)}"
+    return {"value": g_all, "unit": "GLUPS", "cores": used, "kind": "oracle",
+            "sample": (f"FP64 CPU oracle on {lat}: {what}; median of 3 runs of {n_all} steps on {used} "
+                       f"threads (single thread: {n_one} steps)"),
+            "single_thread": {"value": g_one, "unit": "GLUPS", "cores": 1},
+            "cpu_model": info["model"], "host_logical_cpus": info["logical_cpus"],
+            "host_usable_cpus": info["usable_cpus"]}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle, as it stands, on the host cores; each step
+    is one oracle step of the bounded sample the cpu_baseline leg times (all cores)."""
     rank, _, ws = dist_env()
     if rank != 0:
         return
     w = workload(args)
     from oracle import core
-    from paper_2303_08163_gb300 import inputs
-    D = w["D"]
-    dims = (32, 32, 32) if D == 3 else (128, 128, 1)
-    if w["dims"] is None:
-        dims = (64, 64, 1)
+    D, dims, eq, tau, rho, u, what = cpu_sample(w)
     ncell = int(np.prod(dims))
-    rho, u = inputs.random_state(D, dims, seed=5, rho_range=(0.99, 1.01), u_max=0.05)
-    f = core.init(D, dims, w["eq"], rho, u)
-    tau = w["tau"] or 0.8
+    f = core.init(D, dims, eq, rho, u)
+    info = cpu_info()
+    used = core.set_threads(info["usable_cpus"] or 1)
     for _ in range(args.warmup):
-        f = core.step(D, dims, w["eq"], args.bulk, tau, 1, f)
+        f = core.step(D, dims, eq, args.bulk, tau, 1, f)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        f = core.step(D, dims, w["eq"], args.bulk, tau, 1, f)
+        f = core.step(D, dims, eq, args.bulk, tau, 1, f)
     dt = time.perf_counter() - t0
+    core.set_threads(1)
     glups = ncell * args.steps / dt / 1e9
-    sample = (f"each step: one FP64 CPU-oracle step of a {'x'.join(str(d) for d in dims if d > 1)} "
-              f"sample lattice of the workload (single thread)")
+    lat = f"D{D}Q{3 ** D} {'x'.join(str(d) for d in dims if d > 1)}"
+    sample = f"each step: one FP64 CPU-oracle step of {lat} ({what}) on {used} threads"
     line = {"impl": "reference", "metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": w["name"], "sample": sample},
-            "cpu_baseline": {"value": glups, "unit": "GLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": glups, "unit": "GLUPS", "cores": used, "kind": "oracle", "sample": sample,
+                             "cpu_model": info["model"], "host_logical_cpus": info["logical_cpus"]},
             "e2e": {"value": glups, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -325,30 +422,71 @@ def timed_steps(torch, lat, steps, diag_every, stream):
     return evs[0].elapsed_time(evs[-1]), per, diag_steps
 
 
-def velocity_error(torch, lbm, dev, n=128):
-    """Relative L2 velocity error of the F32 and F16S paths against the FP64 path on the
-    D3Q27 n^3 Taylor-Green vortex (Re = 1600) after four convective times."""
+def precision_errors(torch, lbm, dev, n=128, every=5):
+    """Errors of the F32 and F16S storage paths against the FP64 path (equal to the CPU
+    oracle to 1e-12 in the parity tests) on two Taylor-Green cases:
+    (1) D3Q27 n^3 at Re = 1600 over four convective times n / (2 pi u0): the relative L2
+        velocity error at the end, and the relative error of the kinetic-energy decay rate
+        (least-squares slope of -ln E(t) over the window, E from the fused diagnostics
+        every `every` steps);
+    (2) the small D2Q9 configuration (64^2, u0 = 0.05, tau = 0.8, 1000 steps), whose energy
+        decays as exp(-2 nu (k_x^2 + k_y^2) t): the relative error of the fitted rate and the
+        relative L2 velocity error after 1000 steps."""
+    from paper_2303_08163_gb300 import fits, inputs
     u0 = 0.1
     nu = u0 * (n / (2 * math.pi)) / 1600.0
     tau = 0.5 + 3 * nu
     steps = int(round(4 * n / (2 * math.pi * u0)))
     w = dict(name="D3Q27", D=3, dims=(n, n, n), u0=u0)
     rho, u = fields_device(w, torch, dev)
-    out = {}
-    us = {}
+    us, rate = {}, {}
     for prec in (0, 1, 2):
         lat = lbm.Lattice(lbm.D3Q27, (n, n, n), tau, 0, 0, prec)
         lat.init_fields(rho, u, dtype=np.float32)
+        lat.set_option(lbm.OPT_DIAG_EVERY, every)
         lat.step(steps)
         r = torch.empty(n ** 3, device=dev, dtype=torch.float64)
         v = torch.empty(3, n ** 3, device=dev, dtype=torch.float64)
         lat.moments(dtype=np.float64, out=(r, v))
+        hist = lat.diag_history()
+        rate[prec] = fits.energy_decay_rate([h["step"] for h in hist], [h["kinetic"] for h in hist])
         us[prec] = v
         lat.close()
+    out = {"case": f"D3Q27 {n}^3 Taylor-Green, Re=1600, {steps} steps (4 convective times)",
+           "reference": "FP64 GPU path (equal to the CPU oracle to 1e-12 in the parity tests)"}
     for prec in (1, 2):
         out[PREC_NAME[prec]] = float(torch.linalg.norm(us[prec] - us[0]) / torch.linalg.norm(us[0]))
-    out["case"] = f"D3Q27 {n}^3 Taylor-Green, Re=1600, {steps} steps (4 convective times)"
-    out["reference"] = "FP64 GPU path (equal to the CPU oracle to 1e-12 in the parity tests)"
+    out["decay_rate"] = {"definition": "least-squares slope of -ln E(t) over the window, E every "
+                                       f"{every} steps; error = |rate / rate_F64 - 1|",
+                         "F64_per_step": rate[0]}
+    for prec in (1, 2):
+        out["decay_rate"][PREC_NAME[prec]] = abs(rate[prec] / rate[0] - 1)
+    del us
+    torch.cuda.empty_cache()
+    m, tau2, steps2 = 64, 0.8, 1000
+    rho2, u2 = inputs.taylor_green_2d(m, u0=0.05)
+    rate2, vel2 = {}, {}
+    for prec in (0, 1, 2):
+        lat = lbm.Lattice(lbm.D2Q9, (m, m, 1), tau2, 0, 0, prec)
+        lat.set_option(lbm.OPT_DIAG_EVERY, 50)
+        lat.init_fields(rho2, u2)
+        lat.step(steps2 + 1)
+        hist = lat.diag_history()
+        rate2[prec] = fits.energy_decay_rate([h["step"] for h in hist], [h["kinetic"] for h in hist], skip=2)
+        lat.close()
+        lat = lbm.Lattice(lbm.D2Q9, (m, m, 1), tau2, 0, 0, prec)
+        lat.init_fields(rho2, u2)
+        lat.step(steps2)
+        vel2[prec] = lat.moments()[1]
+        lat.close()
+    k = 2 * math.pi / m
+    small = {"case": "D2Q9 64^2 Taylor-Green, u0=0.05, tau=0.8, 1000 steps",
+             "F64_rate_per_step": rate2[0], "theory_2nu_k2": 2 * (tau2 - 0.5) / 3 * 2 * k * k}
+    for prec in (1, 2):
+        small[PREC_NAME[prec]] = {"decay_rate_error": abs(rate2[prec] / rate2[0] - 1),
+                                  "rel_l2_velocity": float(np.linalg.norm(vel2[prec] - vel2[0])
+                                                           / np.linalg.norm(vel2[0]))}
+    out["small_taylor_green_2d"] = small
     return out
 
 
@@ -433,7 +571,7 @@ def run_native(args):
     achieved = algo_bytes / (launch_ms * 1e-3) / 1e9
     info = lat.launch_info()
     kname = "k_step_tma" if info["kernel"] == 2 else "k_step_generic"
-    traffic = ncu_traffic(kname, w["name"], ncell)
+    traffic, traffic_note = ncu_traffic(kname, w["name"], ncell, launch=info)
     glups = aggregate(ws, ncell, args.steps, [t_max])
     # end to end through the C ABI with pinned host buffers
     rho_h = rho.cpu().pin_memory()
@@ -467,17 +605,24 @@ def run_native(args):
         lat.close()
         del lat
         torch.cuda.empty_cache()
-        extras["precision_compare"] = compare_precisions(torch, lbm, dev, w, args, rho, u)
+        extras["precision_compare"] = compare_precisions(torch, lbm, dev, w, args, rho, u,
+                                                         sm_mhz=clocks.get("sm_mhz"))
         if "turbulence" in w["name"]:
             extras["energy_decay"] = energy_decay_compare(torch, lbm, w, args, rho, u)
         elif "shear" in w["name"]:
             extras["divergence"] = shear_divergence(torch, lbm, w, args, rho, u)
         elif w["D"] == 3:
-            extras["l2_velocity_error"] = velocity_error(torch, lbm, dev)
+            errs = precision_errors(torch, lbm, dev)
+            extras["l2_velocity_error"] = {k: v for k, v in errs.items() if k != "small_taylor_green_2d"}
+            extras["decay_rate_error"] = {
+                "taylor_green_3d": {"case": errs["case"], "F32": errs["decay_rate"]["F32"],
+                                    "F16S": errs["decay_rate"]["F16S"],
+                                    "F64_rate_per_step": errs["decay_rate"]["F64_per_step"]},
+                "taylor_green_2d": errs["small_taylor_green_2d"],
+                "definition": errs["decay_rate"]["definition"]}
     cpu = None
     if rank == 0:
-        g, desc = oracle_sample(w, args.cpu_seconds)
-        cpu = {"value": g, "unit": "GLUPS", "cores": 1, "kind": "oracle", "sample": desc}
+        cpu = oracle_baseline(w, args.bulk, seconds=args.cpu_seconds)
     if rank != 0:
         return
     line = {
@@ -491,8 +636,8 @@ def run_native(args):
                    "l2": "inputs larger than L2 (the population array is re-read every step)",
                    "parallelism": "replicas" if ws > 1 else "single GPU", "launch": info},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                     "kernel": kname, "algorithmic_bytes_per_launch": algo_bytes,
+                     "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_note,
+                     "peak_source": peak_src, "kernel": kname, "algorithmic_bytes_per_launch": algo_bytes,
                      "avg_launch_ms": launch_ms},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         "diag_last": {k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in hist[-1].items()} if hist else None,
@@ -627,8 +772,9 @@ def accuracy_gates(torch, lbm, dev, w, args, rho, u):
     return out
 
 
-def compare_precisions(torch, lbm, dev, w, args, rho, u):
-    """Device-timed GLUPS of the same workload in the other storage precisions."""
+def compare_precisions(torch, lbm, dev, w, args, rho, u, sm_mhz=None):
+    """Device-timed GLUPS of the same workload in the other storage precisions (FP64 with
+    its roofline on the FP64 pipe, at the SM clock sampled during the timed region)."""
     out = {}
     D, dims = w["D"], w["dims"]
     ncell = int(np.prod(dims))
@@ -654,8 +800,17 @@ def compare_precisions(torch, lbm, dev, w, args, rho, u):
             e1.synchronize()
             ms = e0.elapsed_time(e1) / steps
             gb = 2 * Q * ESIZE[prec] * ncell / (ms * 1e-3) / 1e9
-            out[key] = {"GLUPS": ncell / (ms * 1e-3) / 1e9, "ms_per_step": ms, "GB_s": gb,
+            glups = ncell / (ms * 1e-3) / 1e9
+            out[key] = {"GLUPS": glups, "ms_per_step": ms, "GB_s": gb,
+                        "hbm_frac": gb / (measured_peaks().get("hbm_gbs") or 6800.0),
                         "launch": lat.launch_info()}
+            if prec == 0:
+                # FP64 collisions are bound by the FP64 pipe (1/64 of the FP32 rate)
+                fpc = fp64_flops_per_cell(w["eq"], bulk, D)
+                peak64 = fp64_peak_gflops(sm_mhz)
+                out[key]["roofline"] = {"bound": "alu", "flops_per_cell_update": fpc,
+                                        "achieved": fpc * glups, "peak": peak64,
+                                        "unit": "GFLOP/s (FP64)", "frac": fpc * glups / peak64}
             lat.close()
             torch.cuda.empty_cache()
     return out
@@ -748,7 +903,7 @@ def batch_mode_sweep(lbm, eq, bulk, steps=4000, every=10, skip_steps=200):
 
 def run_batch(args, w, torch, lbm, dev, rank, ws):
     from paper_2303_08163_gb300 import inputs
-    table = inputs.linear_mode_batch(count=4096, seed=2303)
+    table = inputs.linear_mode_batch(count=args.batch_count, seed=2303)
     count = len(table["nx"])
     dims = np.stack([table["nx"], table["ny"], np.ones(count, dtype=np.int32)], axis=1)
     fields = [inputs.linear_mode_fields(table, k) for k in range(count)]
@@ -759,6 +914,10 @@ def run_batch(args, w, torch, lbm, dev, rank, ws):
     b.init_fields(rho, u)
     b.set_probe(kvec, 10)
     total = int(b.cell_start[-1])
+    if args.shape:
+        b.set_launch_shape(*[int(v) for v in args.shape.split(",")])
+    elif not args.no_tune:
+        b.autotune(steps=10)
     b.step(args.warmup)
     b.sync()
     stream = torch.cuda.current_stream()
@@ -805,24 +964,37 @@ def run_batch(args, w, torch, lbm, dev, rank, ws):
     # cycle x 2 flops x the median SM clock under load
     fpc = fp64_flops_per_cell(w["eq"], args.bulk)
     clocks = clk.summary()
-    sm_ghz = (clocks.get("sm_mhz") or 2070.0) / 1e3
-    fp64_peak = 152 * 2 * 2 * sm_ghz  # GFLOP/s
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    fp64_peak = fp64_peak_gflops(sm_mhz)
     achieved = fpc * glups / ws  # GFLOP/s of one GPU
     hbm = 2 * 9 * 8 * glups / ws  # GB/s of one GPU
-    g, desc = oracle_sample(w, args.cpu_seconds)
+    launch = b.launch_info()
+    rec = [r for r in traffic_records() if r.get("kernel") == "k_step_batch" and r.get("source_hash") == source_hash()
+           and r.get("workload") == w["name"]
+           and all(r.get("launch", {}).get(k) == launch[k] for k in ("threads", "blocks"))]
+    traffic = rec[0]["dram_bytes_per_cell"] * total * args.steps if rec else None
+    pipe = None
+    if rec and rec[0].get("fp64_thread_inst_per_cell"):
+        # the FP64 pipe issues 2 thread instructions per SM per cycle (DADD, DMUL and DFMA
+        # alike), so its roofline counts instructions, not flops
+        ipc = rec[0]["fp64_thread_inst_per_cell"]
+        pipe = {"fp64_thread_inst_per_cell_update": ipc, "achieved_ginst_s": ipc * glups / ws,
+                "peak_ginst_s": 152 * 2 * sm_mhz / 1e3, "frac": ipc * glups / ws / (152 * 2 * sm_mhz / 1e3),
+                "source": rec[0].get("captured_on")}
+    cpu = oracle_baseline(w, args.bulk, seconds=args.cpu_seconds)
     line = {"metric": METRIC, "value": glups, "unit": "GLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w["name"], "total_cells": total, "probe_every": 10,
-                       "launch": b.launch_info()},
+            "config": {"workload": w["name"], "instances": count, "total_cells": total, "probe_every": 10,
+                       "launch": launch, "l2": "inputs larger than L2 (the 4096-instance state is 2.2 GB)"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "GFLOP/s (FP64)",
-                         "frac": achieved / fp64_peak,
-                         "traffic": ncu_traffic("k_step_batch", w["name"], total * args.steps),
+                         "frac": achieved / fp64_peak, "traffic": traffic,
+                         "traffic_source": rec[0].get("captured_on") if rec else
+                         "no ncu record for this kernel source and launch shape",
                          "kernel": "k_step_batch", "launches": 1,
-                         "flops_per_cell_update": fpc,
+                         "flops_per_cell_update": fpc, "fp64_pipe": pipe,
                          "hbm_GB_s": hbm, "hbm_frac": hbm / (measured_peaks().get("hbm_gbs") or 6800.0)},
-            "cpu_baseline": {"value": g, "unit": "GLUPS", "cores": 1, "kind": "oracle", "sample": desc},
-            "e2e": e2e, "gpu_launches": 1, "clocks": clocks}
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 1, "clocks": clocks}
     print(json.dumps(line), flush=True)
 
 

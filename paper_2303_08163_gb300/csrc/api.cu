@@ -446,9 +446,13 @@ int autotune(lbm_ctx *c) {
     if (rc) return rc;
     lbm_ctx *p = px.p;
     p->step = c->step;  // the same AA parity: the copied planes are a consistent layout
-    CK(cudaMemcpy2DAsync(p->lat.A, (size_t)p->lat.plane * es, c->lat.A, (size_t)c->lat.plane * es,
-                         (size_t)p->ncell * es, c->Q, cudaMemcpyDeviceToDevice, c->stream),
-       "tuning proxy fill");
+    // one copy per direction plane (a plane of a large lattice exceeds the pitch limit
+    // of a 2-D copy)
+    for (int i = 0; i < c->Q; ++i)
+        CK(cudaMemcpyAsync(static_cast<char *>(p->lat.A) + (size_t)i * p->lat.plane * es,
+                           static_cast<const char *>(c->lat.A) + (size_t)i * c->lat.plane * es, (size_t)p->ncell * es,
+                           cudaMemcpyDeviceToDevice, c->stream),
+           "tuning proxy fill");
     std::vector<std::vector<int>> cands;
     const int U = 16 / es;
     const int64_t rowb = c->lat.nx * (int64_t)es;

@@ -154,7 +154,7 @@ def random_solenoidal(dims, u_rms=0.05, k_peak=8.0, seed=2303):
     kdotv = (KX * comps[0] + KY * comps[1] + KZ * comps[2]) / np.where(k2 > 0, k2, 1.0)
     comps = [comps[0] - KX * kdotv, comps[1] - KY * kdotv, comps[2] - KZ * kdotv]
     # arrays are indexed [x, y, z]; the library wants x fastest (z, y, x order)
-    u = [np.fft.irfftn(cv, s=(nx, ny, nz)).transpose(2, 1, 0).reshape(-1) for cv in comps]
+    u = [np.fft.irfftn(cv, s=(nx, ny, nz), axes=(0, 1, 2)).transpose(2, 1, 0).reshape(-1) for cv in comps]
     u = np.stack(u)
     scale = u_rms / np.sqrt(np.mean(u * u))
     u *= scale
@@ -250,6 +250,21 @@ def acoustic_wave_1d(nx, U0, drho=1e-3, rho0=1.0, ny=1):
     rho = np.broadcast_to(rho0 + drho * np.sin(2 * math.pi * x / nx), (ny, nx)).reshape(-1)
     ux = np.full(nx * ny, float(U0))
     return rho.copy(), np.stack([ux, np.zeros(nx * ny)])
+
+
+def random_state_torch(D, dims, seed, rho_range=(0.8, 1.2), u_max=0.2, device="cuda"):
+    """Uniform random rho and u drawn independently for every cell, as float32 tensors on
+    `device` (rho (ncell,), u (D, ncell), x fastest), from a seeded torch generator: the
+    non-smooth field of the full-size parity checks, built without a host copy."""
+    import torch
+    n = int(np.prod(dims))
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    rho = torch.rand(n, generator=gen, device=device, dtype=torch.float32)
+    rho.mul_(rho_range[1] - rho_range[0]).add_(rho_range[0])
+    u = torch.rand(D, n, generator=gen, device=device, dtype=torch.float32)
+    u.mul_(2 * u_max).sub_(u_max)
+    return rho, u
 
 
 def random_state(D, dims, seed, rho_range=(0.8, 1.2), u_max=0.2):

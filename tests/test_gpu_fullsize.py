@@ -11,33 +11,29 @@ autotuned one), on outputs the oracle can compute one by one:
   2 steps.
 - The largest lattice: 1304^3 cells (more than 2^31), binary16, both step kernels.
 
-Tolerances for stored binary16 / FP32 values: each storage rounding moves f - w rho0 by
-at most half an ulp (u = 2^-11 resp. 2^-24 relative; below 2^-14 a binary16 value is a
-subnormal, rounded to a multiple of 2^-24, an absolute error of up to 2^-25).  A sampled
-value after n steps has been rounded n + 1 times directly; the roundings of the other
-populations reach it through rho and u, to first order amplified by at most omega K
-(omega = 1/tau, K the bound of `sensitivity` on |d f^eq_i / d f_j| / w_i at the field's
-largest |u_a|); the FP32 collision is a chain of at most 32 roundings of operands bounded
-by w_i (1 + S).  So, with S = sum_j |f_j - w_j|,
-|f_gpu - f_ref| <= (n + 2) [u (|f_i - w_i| + omega K w_i S) + 2^-25 (1 + omega K Q w_i)]
-                   + 32 n 2^-24 w_i (1 + S) (1 + omega K)
-(the 2^-25 term for binary16 only).  Data-movement errors (a wrong neighbour, direction or
-layout) are of order w_i |u| and stay well outside this bound.
+- The same 512^3 lattice filled with a field that varies from cell to cell (uniform
+  random rho and u per cell), binary16 and FP32: sampled cells after 1 and 2 steps.  On
+  the smooth vortex a wrong-neighbour read changes a population by about w_i |grad u|,
+  which lies inside the rounding bound; on this field it changes it by about
+  w_i |delta rho + 3 delta u|, far outside (tests/test_fullsize_power.py shows both on the
+  CPU with the oracle).
+- The autotuned TMA kernel against the one-cell kernel at 512^3 (binary16 and FP32) and on
+  the 1024 x 512 x 512 turbulence box (binary16): the stored states after 1, 2 and 3 steps
+  are identical bit for bit (both kernels evaluate the same collision on the same stored
+  values, so any data-movement error shows up as a difference).
+
+The rounding bound of the sampled checks is derived in tests/fullsize_bounds.py.
 """
 import math
 
 import numpy as np
 import pytest
 
+from fullsize_bounds import UNIT, sampled_tolerance
 from oracle import core
 from paper_2303_08163_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
-
-UNIT = {1: 2.0 ** -24, 2: 2.0 ** -11}
-# half the spacing of the subnormal numbers: below 2^-14 a binary16 store rounds to a
-# multiple of 2^-24, an absolute error of up to 2^-25 that no relative bound covers
-FLOOR = {1: 0.0, 2: 2.0 ** -25}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -63,30 +59,13 @@ def flat(cells, dims):
     return cells[:, 0] + nx * (cells[:, 1] + ny * cells[:, 2])
 
 
-def sensitivity(D, umax, rho_min=0.9):
-    """Bound K on |d f^eq_i / d f_j| / w_i for |u_a| <= umax, rho >= rho_min: f^eq_i =
-    w_i rho (1 + h_i(u)) with u = j / rho, so a change of f_j moves f^eq_i through rho
-    (factor 1 + |h_i|) and through u (factor sum_a |dh_i/du_a| (1 + |u_a|) / rho).  For the
-    entropic and product forms h_i = prod_a t_a - 1 with t <= 1 + 3u + 3u^2 and |dt/du| <=
-    3 + 6u; for the quadratic form |dh/du_a| <= 3 + 9 D u + 3u."""
-    t = 1 + 3 * umax + 3 * umax ** 2
-    hmax = max(t ** D - 1, 3 * D * umax + 4.5 * (D * umax) ** 2 + 1.5 * D * umax ** 2)
-    g = max((3 + 6 * umax) * t ** (D - 1), 3 + 9 * D * umax + 3 * umax)
-    return 1 + hmax + D * g * (1 + umax) / rho_min
-
-
-def check_sampled(lat, D, dims, eq, bulk, tau, prec, rho_fn, u_fn, nsteps, cells, umax):
+def check_sampled(lat, D, dims, eq, bulk, tau, prec, rho_fn, u_fn, nsteps, cells, umax, rho_min=0.9):
     got = lat.sample_populations(flat(cells, dims))
     ref = core.local_populations(D, dims, eq, bulk, tau, nsteps, rho_fn, u_fn, cells)
     _, w = core.lattice(D)
-    shifted = np.abs(ref - w)
-    S = shifted.sum(axis=1, keepdims=True)
     # storage roundings of this population, plus those reaching it through rho and u
     # (first order, amplified by at most omega K), plus the FP32 collision arithmetic
-    ok = (1.0 / tau) * sensitivity(D, umax)
-    tol = ((nsteps + 2) * UNIT[prec] * (shifted + ok * w * S)
-           + (nsteps + 2) * FLOOR[prec] * (1 + ok * w * len(w))
-           + 32 * nsteps * 2.0 ** -24 * w * (1 + S) * (1 + ok))
+    tol = sampled_tolerance(ref, w, D, tau, prec, nsteps, umax, rho_min)
     bad = np.abs(got - ref) > tol
     assert not bad.any(), f"{bad.sum()} sampled populations off; worst {np.max(np.abs(got - ref) - tol):.3e}"
 
@@ -247,6 +226,105 @@ def test_turbulence_1024x512x512_sampled(prec):
     check_sampled(lat, 3, dims, core.EQ_ENTROPIC, 0, tau, prec, rho_fn, u_fn, 1, cells, umax)
     lat.step(1)
     check_sampled(lat, 3, dims, core.EQ_ENTROPIC, 0, tau, prec, rho_fn, u_fn, 2, cells, umax)
+    lat.close()
+    del rho, u
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("case,prec", [("tgv512", 2), ("tgv512", 1), ("turb", 2)])
+def test_fullsize_tma_equals_one_cell_bitwise(case, prec):
+    """At the full benchmark sizes and in the autotuned launch shape (whatever it is on
+    this device: rows per job, segments, stages, threads, the paired binary16 body), the
+    TMA kernel's stored state equals the one-cell kernel's bit for bit after 1, 2 and 3
+    steps (Eq. 1: collide, then stream; both kernels evaluate the same collision on the
+    same stored values, so only a data-movement error can make them differ).  The tuner
+    must also leave the state it was called on untouched."""
+    import torch
+    from paper_2303_08163_gb300 import lbm
+    if case == "tgv512":
+        n, u0 = 512, 0.1
+        dims = (n, n, n)
+        tau = 0.5 + 3 * u0 * (n / (2 * math.pi)) / 1600.0
+        rho, u = inputs.taylor_green_3d_torch(n, u0=u0, device="cuda")
+    else:
+        dims = (1024, 512, 512)
+        tau = 0.5 + 1e-4
+        rho, u = inputs.random_solenoidal_torch(dims, u_rms=0.05, device="cuda")
+    ncell = int(np.prod(dims))
+    store = {1: torch.int32, 2: torch.int16}[prec]
+    a = lbm.Lattice(lbm.D3Q27, dims, tau, lbm.ENTROPIC, 0, prec)
+    a.init_fields(rho, u, dtype=np.float32)
+    before = torch.empty(27 * ncell, dtype=store, device="cuda")
+    a.get_populations("storage", out=before)
+    a.set_option(lbm.OPT_TUNE, 1)  # the benchmark's launch shape
+    after = torch.empty_like(before)
+    a.get_populations("storage", out=after)
+    assert torch.equal(before, after), "the tuner changed the state"
+    assert a.step_count == 0
+    del before
+    info = a.launch_info()
+    print(f"{case} prec={prec}: tuned shape {info}")
+    assert info["kernel"] == lbm.KERNEL_TMA
+    b = lbm.Lattice(lbm.D3Q27, dims, tau, lbm.ENTROPIC, 0, prec)
+    b.set_launch_shape(lbm.KERNEL_GENERIC, 256)
+    b.init_fields(rho, u, dtype=np.float32)
+    del rho, u
+    torch.cuda.empty_cache()
+    other = torch.empty_like(after)
+    for n in (1, 2, 3):
+        a.step(1)
+        b.step(1)
+        a.get_populations("storage", out=after)
+        b.get_populations("storage", out=other)
+        same = torch.equal(after, other)
+        if not same:
+            idx = torch.nonzero(after != other)[:4].flatten().tolist()
+            raise AssertionError(f"after {n} steps the kernels differ at flat indices {idx} "
+                                 f"(direction = index // {ncell})")
+    a.sync()
+    b.sync()
+    for x in (a, b):
+        x.close()
+    del after, other
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec", [2, 1])
+def test_512_nonsmooth_field_sampled(prec):
+    """512^3 lattice in the autotuned shape, filled with uniform random rho in [0.9, 1.1]
+    and u_a in [-0.1, 0.1] drawn independently for every cell (a seeded generator on the
+    device), tau of the Re = 1600 vortex: sampled cells after 1 and 2 steps against the
+    oracle, which starts from the same generated values (gathered at each patch).  Here a
+    wrong neighbour, direction or layout moves a population far outside the rounding bound."""
+    import torch
+    from paper_2303_08163_gb300 import lbm
+    n, u0 = 512, 0.1
+    dims = (n, n, n)
+    nx, ny, _ = dims
+    tau = 0.5 + 3 * u0 * (n / (2 * math.pi)) / 1600.0
+    rho, u = inputs.random_state_torch(3, dims, seed=512 + prec, rho_range=(0.9, 1.1), u_max=0.1,
+                                       device="cuda")
+
+    def gather(t, ix, iy, iz):
+        idx = torch.from_numpy(np.ascontiguousarray(ix + nx * (iy + ny * iz), dtype=np.int64).reshape(-1))
+        return t[..., idx.to(t.device)].double().cpu().numpy()
+
+    def rho_fn(ix, iy, iz):
+        return gather(rho, ix, iy, iz).reshape(np.shape(ix))
+
+    def u_fn(ix, iy, iz):
+        return gather(u, ix, iy, iz).reshape((3,) + np.shape(ix))
+
+    lat = lbm.Lattice(lbm.D3Q27, dims, tau, lbm.ENTROPIC, 0, prec)
+    lat.init_fields(rho, u, dtype=np.float32)
+    lat.set_option(lbm.OPT_TUNE, 1)
+    assert lat.launch_info()["kernel"] == lbm.KERNEL_TMA
+    cells = sample_cells(dims, 40, seed=77 + prec)
+    lat.step(1)
+    # bounds of the field a step or two later: |u_a| <= 0.12, rho >= 0.85
+    check_sampled(lat, 3, dims, core.EQ_ENTROPIC, 0, tau, prec, rho_fn, u_fn, 1, cells, 0.12, rho_min=0.85)
+    lat.step(1)
+    check_sampled(lat, 3, dims, core.EQ_ENTROPIC, 0, tau, prec, rho_fn, u_fn, 2, cells, 0.12, rho_min=0.85)
     lat.close()
     del rho, u
     torch.cuda.empty_cache()

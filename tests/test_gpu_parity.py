@@ -88,6 +88,52 @@ def test_taylor_green_64_fp64_1000_steps(kernel):
     lat.close()
 
 
+# D3Q27 FP64 over 1000 steps: (name, dims, fields, tau, launch shapes).  The TMA shapes
+# cover several whole rows per job with a ragged last row group (y wrap) and aligned
+# row segments with halos; the one-cell kernel is the second path.
+D3Q27_1000 = [
+    ("taylor-green 16^3", (16, 16, 16), "tgv", 0.8,
+     [(2, 128, 3, 4, 16, 1024), (1, 256)]),
+    ("random 12x10x8", (12, 10, 8), "random", 0.6,
+     [(2, 128, 2, 3, 12, 1024), (2, 128, 2, 1, 4, 1024), (1, 128)]),
+]
+
+
+@pytest.mark.parametrize("name,dims,field,tau,shapes", D3Q27_1000, ids=[c[0] for c in D3Q27_1000])
+@pytest.mark.parametrize("bulk", [0, 1])
+def test_d3q27_fp64_1000_steps(name, dims, field, tau, shapes, bulk):
+    """D3Q27, entropic equilibrium (Eq. eq:Entropic_isothermal_EDF), bulk correction off
+    and on (Eq. eq:redefined_relaxation rate), FP64: after 1000 steps every population of
+    every kernel path equals the oracle's to 1e-12 (maximum relative error), and again one
+    step later (the other AA layout)."""
+    import os
+    lbm = lbm_mod()
+    n = int(np.prod(dims))
+    if field == "tgv":
+        rho, u = inputs.taylor_green_3d(dims[0], u0=0.05)
+    else:
+        rho, u = inputs.random_state(3, dims, seed=1000 + bulk, rho_range=(0.9, 1.1), u_max=0.1)
+    assert rho.shape == (n,)
+    core.set_threads(os.cpu_count() or 1)  # the same result bit for bit as one thread
+    try:
+        ref = run_oracle(3, dims, core.EQ_ENTROPIC, bulk, tau, rho, u, 1000)
+        ref1 = core.step(3, dims, core.EQ_ENTROPIC, bulk, tau, 1, ref)
+    finally:
+        core.set_threads(1)
+    for shape in shapes:
+        lat = lbm.Lattice(lbm.D3Q27, dims, tau, lbm.ENTROPIC, bulk, lbm.F64)
+        lat.set_launch_shape(*shape)
+        assert lat.launch_info()["kernel"] == shape[0]
+        lat.init_fields(rho, u)
+        lat.step(1000)
+        err = max_rel(lat.get_populations(), ref)
+        lat.step(1)
+        err1 = max_rel(lat.get_populations(), ref1)
+        print(f"{name} bulk={bulk} shape={shape}: max rel error {err:.2e} (1000 steps), {err1:.2e} (1001)")
+        assert err <= 1e-12 and err1 <= 1e-12
+        lat.close()
+
+
 # (D, dims, launch shape) covering: whole rows with several rows per job and y wrap,
 # aligned segments with halos and a shorter last segment, ragged Nx (generic only).
 SHAPES = [
@@ -245,6 +291,63 @@ def test_fused_diagnostics_match_oracle():
     lat.close()
 
 
+DIAG_CASES = [
+    (2, (64, 64, 1), None),
+    (2, (64, 64, 1), (1, 256)),
+    (3, (24, 20, 12), None),
+    (3, (24, 20, 12), (2, 128, 2, 2, 24, 2048)),
+    (3, (24, 20, 12), (1, 128)),
+]
+
+
+@pytest.mark.parametrize("D,dims,shape", DIAG_CASES)
+@pytest.mark.parametrize("prec", [1, 2])
+def test_fused_diagnostics_reduced_precision(D, dims, shape, prec):
+    """Fused diagnostics of the FP32 and binary16 paths (every kernel, the paired binary16
+    body included) against the oracle's compensated sums over the same state (exported as
+    FP64 at the step the record describes): mass and momentum (the conservation
+    constraints of Sec. II), kinetic energy, max |u_a|.  The kernels form each cell's
+    moments in FP32 from its Q stored values (up to Q roundings of terms bounded by
+    S_c = sum_i |f_i - w_i rho0|) and add at most 128 cells in FP32 before an FP64 sum, so
+    |sum_gpu - sum_ref| <= 2^-24 (Q + 128) sum_c S_c for mass and momentum; the kinetic
+    energy gets 2^-24 [(Q + 138) E + Q sum_c |u_c| S_c] (the FP32 u = j / rho and the
+    products), max |u| 2^-24 Q max_c S_c / rho + 4 ulp; everything twice for safety.  A
+    missed or doubled cell changes the mass by about rho, far outside these bounds."""
+    lbm = lbm_mod()
+    Q = 3 ** D
+    if D == 2:
+        rho, u = inputs.taylor_green_2d(dims[0], u0=0.08)
+    else:
+        rho, u = inputs.random_state(3, dims, seed=41 + prec, rho_range=(0.9, 1.1), u_max=0.1)
+    lat = lbm.Lattice(lbm.D2Q9 if D == 2 else lbm.D3Q27, dims, 0.6, lbm.ENTROPIC, 1, prec)
+    if shape is not None:
+        lat.set_launch_shape(*shape)
+    lat.set_option(lbm.OPT_DIAG_EVERY, 3)
+    lat.init_fields(rho, u)
+    f0 = lat.get_populations()
+    lat.step(6)
+    f6 = lat.get_populations()
+    lat.step(1)
+    hist = lat.diag_history()
+    assert [h["step"] for h in hist] == [0, 3, 6]
+    _, w = core.lattice(D)
+    eps = 2.0 ** -24
+    for h, f in ((hist[0], f0), (hist[2], f6)):
+        d = core.diagnostics(D, dims, f)
+        S = np.abs(f - w[:, None]).sum(axis=0)
+        r, v = core.moments(D, dims, f)
+        speed = np.sqrt((v ** 2).sum(axis=0))
+        tol_m = 2 * eps * (Q + 128) * S.sum() + 1e-13 * d["mass"]
+        tol_e = 2 * eps * ((Q + 138) * d["kinetic"] + Q * (speed * S).sum())
+        tol_u = 2 * eps * Q * (S / r).max() + 4 * eps * d["max_u"]
+        assert h["nonfinite"] == 0
+        assert abs(h["mass"] - d["mass"]) <= tol_m, (h["mass"], d["mass"], tol_m)
+        assert np.all(np.abs(h["momentum"] - d["momentum"]) <= tol_m), (h["momentum"], d["momentum"], tol_m)
+        assert abs(h["kinetic"] - d["kinetic"]) <= tol_e, (h["kinetic"], d["kinetic"], tol_e)
+        assert abs(h["max_u"] - d["max_u"]) <= tol_u, (h["max_u"], d["max_u"], tol_u)
+    lat.close()
+
+
 def test_nonfinite_state_is_reported():
     """A NaN population (fault injected on the host through lbm_set_populations) makes
     the next fused diagnostics return LBM_ENONFINITE; the object stays usable."""
@@ -315,11 +418,96 @@ def test_invalid_launch_shape_is_rejected():
     with pytest.raises(lbm.LBMError):
         lat.set_launch_shape(2, 256, 9, 1, 40, 1024)  # too many stages
     lat.close()
+    lat = lbm.Lattice(lbm.D2Q9, (40, 8, 1), 0.8, lbm.ENTROPIC, 0, lbm.F32)
+    before = lat.launch_info()
+    bad = [(2, 256, 3, 1, 0, 1024),            # empty segment
+           (2, 256, 3, 1, -8, 1024),           # negative segment
+           (2, 512, 3, 1, 40, 1024),           # 512 threads: binary16 D2Q9 only
+           (2, 2 ** 32 + 64, 3, 1, 40, 1024),  # would wrap to 64 in 32 bits
+           (2, 256, 2 ** 32 + 3, 1, 40, 1024),
+           (1, 2 ** 32 + 128)]
+    for shape in bad:
+        with pytest.raises(lbm.LBMError) as e:
+            lat.set_launch_shape(*shape)
+        assert e.value.status == lbm.EINVAL, shape
+    assert lat.launch_info() == before
+    lat.close()
     lat = lbm.Lattice(lbm.D2Q9, (13, 8, 1), 0.8, lbm.ENTROPIC, 0, lbm.F32)
     assert lat.launch_info()["kernel"] == lbm.KERNEL_GENERIC  # 52-byte rows: no TMA
     with pytest.raises(lbm.LBMError):
         lat.set_launch_shape(2, 256, 3, 1, 13, 1024)
     lat.close()
+
+
+def test_512_thread_shape_d2q9_binary16():
+    """D2Q9 with binary16 storage accepts up to 512 colliding threads per block (the
+    tuner's candidates); the state equals the one-cell kernel's bit for bit."""
+    lbm = lbm_mod()
+    dims = (256, 40, 1)
+    rho, u = inputs.random_state(2, dims, seed=88, u_max=0.1)
+    lats = []
+    for shape in ((2, 512, 2, 4, 256, 2048), (1, 256)):
+        lat = lbm.Lattice(lbm.D2Q9, dims, 0.57, lbm.ENTROPIC, 1, lbm.F16S)
+        lat.set_launch_shape(*shape)
+        lat.init_fields(rho, u)
+        lats.append(lat)
+    assert lats[0].launch_info()["threads"] == 512
+    for n in (1, 2):
+        for lat in lats:
+            lat.step(1)
+        a, b = (lat.get_populations("storage") for lat in lats)
+        assert np.array_equal(a.view(np.uint16), b.view(np.uint16)), f"differ after {n} steps"
+    for lat in lats:
+        lat.close()
+
+
+_TUNE_CACHE_CHILD = r"""
+import sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_2303_08163_gb300 import lbm, inputs
+lbm.load()
+dims = (24, 10, 6)
+lat = lbm.Lattice(lbm.D3Q27, dims, 0.57, lbm.ENTROPIC, 0, lbm.F16S)
+info = lat.launch_info()
+ref = lbm.Lattice(lbm.D3Q27, dims, 0.57, lbm.ENTROPIC, 0, lbm.F16S)
+ref.set_launch_shape(1, 128)
+rho, u = inputs.random_state(3, dims, seed=5, u_max=0.1)
+for x in (lat, ref):
+    x.init_fields(rho, u)
+    x.step(3)
+same = np.array_equal(lat.get_populations("storage").view(np.uint16), ref.get_populations("storage").view(np.uint16))
+print("RESULT", info["kernel"], info["stages"], info["smem_bytes"], int(same))
+"""
+
+
+def test_bad_tune_cache_entries_are_rejected(tmp_path):
+    """Launch shapes remembered in the LBM_TUNE_CACHE file are checked against the lattice
+    and the device before use: an entry with too many stages, or whose shared-memory size
+    does not match its shape, is ignored (the default shape is used instead), so an edited
+    or stale file cannot make a kernel overrun its shared memory."""
+    import os
+    import subprocess
+    import sys
+    import torch
+    lbm = lbm_mod()
+    ver = lbm.load().lbm_version()
+    name = torch.cuda.get_device_name(0).replace(" ", "_")
+    key = f"v{ver}|{name}|D3|P2|E0|B0|24x10x6"
+    for rec in ("2 256 152 20 1 24 1024 552960",   # 20 stages: past the barrier arrays
+                "2 256 152 3 3 24 1024 9999",      # shared memory does not match the shape
+                "2 256 152 3 1 6 1024 82944"):     # 6-cell segments: not whole 16-byte units
+        path = tmp_path / "tune.txt"
+        path.write_text(f"{key} {rec}\n")
+        root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+        env = dict(os.environ, LBM_TUNE_CACHE=str(path))
+        r = subprocess.run([sys.executable, "-c", _TUNE_CACHE_CHILD, root], capture_output=True, text=True,
+                           env=env, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        line = [x for x in r.stdout.splitlines() if x.startswith("RESULT")][-1].split()
+        kernel, stages, smem, same = (int(v) for v in line[1:])
+        assert (stages, smem) not in ((20, 552960), (3, 9999), (3, 82944)), line
+        assert same == 1
 
 
 # ------------------------------------------------------------------------------- batch
@@ -390,6 +578,48 @@ def test_batch_d3q27_parity_and_probes():
             ncell = int(c1 - c0)
             assert np.all(np.abs(series[k] - sk) <= 1e-12 * np.abs(sk) + 1e-13 * ncell)
         b.close()
+
+
+def test_batch_autotune_keeps_state_and_parity():
+    """lbm_batch_autotune changes only the launch shape: the populations, the step counter,
+    the status and the recorded probe samples are unchanged, and stepping on with the
+    chosen shape still matches the oracle (populations and probes to 1e-12).  Invalid
+    shapes are rejected."""
+    lbm = lbm_mod()
+    table = inputs.linear_mode_batch(count=40, seed=21, nmin=6, nmax=48)
+    count = len(table["nx"])
+    dims = np.stack([table["nx"], table["ny"], np.ones(count, dtype=np.int32)], axis=1)
+    fields = [inputs.linear_mode_fields(table, k) for k in range(count)]
+    rho = np.concatenate([f[0] for f in fields])
+    u = np.concatenate([f[1].reshape(-1) for f in fields])
+    kvec = np.stack([table["nmode"], np.zeros(count, np.int32), np.zeros(count, np.int32)], axis=1)
+    b = lbm.Batch(lbm.D2Q9, dims, table["tau"], core.EQ_ENTROPIC, 1)
+    b.init_fields(rho, u)
+    b.set_probe(kvec, 4)
+    b.step(9)
+    before, series0, st0 = b.get_populations(), b.probe_series(), b.status()
+    b.autotune(steps=6)
+    info = b.launch_info()
+    assert info["threads"] in (64, 128, 256) and 1 <= info["blocks"] <= count
+    assert b.info()["step"] == 9
+    assert np.array_equal(b.get_populations(), before)
+    assert np.array_equal(b.probe_series(), series0) and np.array_equal(b.status(), st0)
+    b.step(14)
+    series, pops = b.probe_series(), b.get_populations()
+    for k in range(count):
+        d3 = (int(dims[k, 0]), int(dims[k, 1]), 1)
+        f0 = core.init(2, d3, core.EQ_ENTROPIC, fields[k][0], fields[k][1])
+        fk, sk = core.run_probed(2, d3, core.EQ_ENTROPIC, 1, float(table["tau"][k]), 23, 4, tuple(kvec[k]), f0)
+        c0, c1 = b.cell_start[k], b.cell_start[k + 1]
+        assert max_rel(pops[9 * c0: 9 * c1].reshape(9, -1), fk) <= 1e-12
+        assert np.all(np.abs(series[k] - sk) <= 1e-12 * np.abs(sk) + 1e-13 * int(c1 - c0))
+    for threads, blocks in ((48, 4), (512, 4), (128, 0), (128, count + 1)):
+        with pytest.raises(lbm.LBMError) as e:
+            b.set_launch_shape(threads, blocks)
+        assert e.value.status == lbm.EINVAL
+    b.set_launch_shape(64, count)  # one instance per block
+    assert b.launch_info()["blocks"] == count
+    b.close()
 
 
 # ------------------------------------------------------------------- degenerate states

@@ -54,6 +54,38 @@ def test_taylor_green_64_energy_decay_rate():
     lat.close()
 
 
+@pytest.mark.parametrize("prec,tol", [(1, 1e-4), (2, 1e-3)])
+def test_decay_rate_error_per_precision(prec, tol):
+    """The small Taylor-Green configuration (D2Q9 64^2, u0 = 0.05, tau = 0.8, 1000 steps):
+    the kinetic-energy decay rate of the FP32 and binary16 storage paths, fitted as for
+    the FP64 check above (E(t) ~ exp(-2 nu (k_x^2 + k_y^2) t)), against the same fit of
+    the FP64 oracle's energies.  The bound on the relative rate error is the velocity-error
+    tolerance of each path (1e-4 FP32, 1e-3 binary16)."""
+    from paper_2303_08163_gb300 import lbm
+    n, tau, steps, every = 64, 0.8, 1000, 50
+    dims = (n, n, 1)
+    rho, u = inputs.taylor_green_2d(n, u0=0.05)
+    lat = lbm.Lattice(lbm.D2Q9, dims, tau, lbm.ENTROPIC, 0, prec)
+    lat.set_option(lbm.OPT_DIAG_EVERY, every)
+    lat.init_fields(rho, u)
+    lat.step(steps + 1)
+    hist = lat.diag_history()
+    lat.close()
+    t = np.array([h["step"] for h in hist], dtype=float)
+    e = np.array([h["kinetic"] for h in hist])
+    f = core.init(2, dims, core.EQ_ENTROPIC, rho, u)
+    e_ref = [core.diagnostics(2, dims, f)["kinetic"]]
+    for _ in range(steps // every):
+        f = core.step(2, dims, core.EQ_ENTROPIC, 0, tau, every, f)
+        e_ref.append(core.diagnostics(2, dims, f)["kinetic"])
+    assert list(t) == [every * q for q in range(len(e_ref))]
+    rate = fits.energy_decay_rate(t, e, skip=2)
+    ref = fits.energy_decay_rate(t, np.array(e_ref), skip=2)
+    err = abs(rate / ref - 1)
+    print(f"prec={prec}: decay rate {rate:.8e} vs oracle {ref:.8e}, relative error {err:.2e}")
+    assert err <= tol
+
+
 def _batch(lbm, table, eq, bulk, every_k, steps):
     count = len(table["nx"])
     dims = np.stack([table["nx"], table["ny"], np.ones(count, dtype=np.int32)], axis=1)
@@ -100,12 +132,16 @@ def test_batched_modes_match_von_neumann(eq):
 
 
 def test_paper_pressure_wave_experiment():
-    """Sec. V.B.2: effective viscosity vs U0 from the energy decay of a 1-D pressure wave."""
+    """Sec. V.B.2: effective viscosity vs U0 in [-0.3, 0.3] from the energy decay of a 1-D
+    pressure wave.  The run at -U0 is the mirror image (x -> -x) of the run at U0 shifted
+    by half a box (the mirror of rho = 1 + drho sin(k x) is 1 - drho sin(k x), i.e. the same
+    wave translated by N/2), so its energy history, and the fitted viscosity, must be the
+    same up to rounding."""
     from paper_2303_08163_gb300 import lbm
     nx, nu = 128, 0.05
     tau = 0.5 + 3 * nu
     k = 2 * math.pi / nx
-    U0s = [0.0, 0.1, 0.2, 0.3]
+    U0s = [-0.3, -0.2, -0.1, 0.0, 0.1, 0.2, 0.3]
     rows = []
     nu_eff = {}
     for eq in (core.EQ_ENTROPIC, core.EQ_PRODUCT):
@@ -128,10 +164,15 @@ def test_paper_pressure_wave_experiment():
     print("eq bulk U0 nu_eff(fit) nu_eff(von Neumann)")
     for r in rows:
         print(f"{r[0]} {r[1]} {r[2]:.1f} {r[3]:.5f} {r[4]:.5f}")
-    for U0 in (0.2, 0.3):
+    for U0 in (-0.3, -0.2, 0.2, 0.3):
         for eq in (core.EQ_ENTROPIC, core.EQ_PRODUCT):
             assert abs(nu_eff[(eq, 1, U0)] - nu) < abs(nu_eff[(eq, 0, U0)] - nu)
         assert abs(nu_eff[(core.EQ_PRODUCT, 0, U0)] - nu) > abs(nu_eff[(core.EQ_ENTROPIC, 0, U0)] - nu)
+    for eq in (core.EQ_ENTROPIC, core.EQ_PRODUCT):
+        for bulk in (0, 1):
+            for U0 in (0.1, 0.2, 0.3):
+                a, b = nu_eff[(eq, bulk, U0)], nu_eff[(eq, bulk, -U0)]
+                assert abs(a - b) <= 1e-7 * abs(a), (eq, bulk, U0, a, b)
 
 
 def test_turbulence_energy_decay_f16s_vs_f32():

@@ -60,4 +60,10 @@ def test_noalloc_diagnostics_match_existing_entry_point(lattice, dims, prec):
     with pytest.raises(lbm.LBMError) as e:
         lbm.diagnostics_noalloc(lattice, dims, f, out, blocks=1025)
     assert e.value.status == lbm.EINVAL
+    # sizes beyond lbm_create's limits (a dimension above 2^30, or a cell count that
+    # overflows 64 bits) are rejected before anything is launched
+    for bad in ((1 << 31, 4, 4), (1 << 30, 1 << 30, 1 << 30)):
+        with pytest.raises(lbm.LBMError) as e:
+            lbm.diagnostics_noalloc(lbm.D3Q27, bad, f, out, blocks=64)
+        assert e.value.status == lbm.EINVAL
     lat.close()
