@@ -385,11 +385,12 @@ def run_reference(args):
     f = core.init(D, dims, eq, rho, u)
     info = cpu_info()
     used = core.set_threads(info["usable_cpus"] or 1)
-    for _ in range(args.warmup):
-        f = core.step(D, dims, eq, args.bulk, tau, 1, f)
+    # W warm-up steps, then exactly K timed steps, each run as one oracle call (the
+    # wrapper copies the state once per call, not once per step)
+    if args.warmup > 0:
+        f = core.step(D, dims, eq, args.bulk, tau, args.warmup, f)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        f = core.step(D, dims, eq, args.bulk, tau, 1, f)
+    f = core.step(D, dims, eq, args.bulk, tau, args.steps, f)
     dt = time.perf_counter() - t0
     core.set_threads(1)
     glups = ncell * args.steps / dt / 1e9
@@ -481,6 +482,8 @@ def precision_errors(torch, lbm, dev, n=128, every=5):
         lat.close()
     k = 2 * math.pi / m
     small = {"case": "D2Q9 64^2 Taylor-Green, u0=0.05, tau=0.8, 1000 steps",
+             "definition": "least-squares slope of -ln E(t), E every 50 steps from step 100; "
+                           "error = |rate / rate_F64 - 1|",
              "F64_rate_per_step": rate2[0], "theory_2nu_k2": 2 * (tau2 - 0.5) / 3 * 2 * k * k}
     for prec in (1, 2):
         small[PREC_NAME[prec]] = {"decay_rate_error": abs(rate2[prec] / rate2[0] - 1),
@@ -582,23 +585,32 @@ def run_native(args):
     lat.init_fields(rho_h, u_h, dtype=np.float32)
     lat.moments(dtype=np.float32, out=(rout, uout))
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(stream)
     lat.init_fields(rho_h, u_h, dtype=np.float32)
+    ev[1].record(stream)
     lat.step(args.steps)
+    ev[2].record(stream)
     lat.moments(dtype=np.float32, out=(rout, uout))
-    e1.record(stream)
-    e1.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
+    ev[3].record(stream)
+    ev[3].synchronize()
+    e2e_ms = ev[0].elapsed_time(ev[3])
+    in_ms, steps_ms, out_ms = (ev[q].elapsed_time(ev[q + 1]) for q in range(3))
     if ws > 1:
         import torch.distributed as dist
         t = torch.tensor([e2e_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
+    h2d_bytes = (rho_h.numel() + u_h.numel()) * 4
+    d2h_bytes = (rout.numel() + uout.numel()) * 4
     e2e = {"value": ws * ncell * args.steps / (e2e_ms * 1e-3) / 1e9, "unit": "GLUPS",
-           "h2d_bytes_per_step": (rho_h.numel() + u_h.numel()) * 4 / args.steps,
-           "d2h_bytes_per_step": (rout.numel() + uout.numel()) * 4 / args.steps,
-           "path": "lbm_init_fields(host) + lbm_step(K) + lbm_moments(host), pinned buffers"}
+           "h2d_bytes_per_step": h2d_bytes / args.steps,
+           "d2h_bytes_per_step": d2h_bytes / args.steps,
+           "path": "lbm_init_fields(host) + lbm_step(K) + lbm_moments(host), pinned buffers",
+           # where the time goes: the field upload and the moment download run at the
+           # host link's bandwidth (copy plus the init / moments kernel)
+           "breakdown_ms": {"init_fields_from_host": in_ms, "steps": steps_ms, "moments_to_host": out_ms},
+           "host_link_GB_s": {"h2d": h2d_bytes / (in_ms * 1e-3) / 1e9, "d2h": d2h_bytes / (out_ms * 1e-3) / 1e9}}
     launches = args.steps + len(diag_steps)
     extras = {}
     if not args.no_extras and rank == 0:
@@ -617,9 +629,9 @@ def run_native(args):
             extras["decay_rate_error"] = {
                 "taylor_green_3d": {"case": errs["case"], "F32": errs["decay_rate"]["F32"],
                                     "F16S": errs["decay_rate"]["F16S"],
-                                    "F64_rate_per_step": errs["decay_rate"]["F64_per_step"]},
-                "taylor_green_2d": errs["small_taylor_green_2d"],
-                "definition": errs["decay_rate"]["definition"]}
+                                    "F64_rate_per_step": errs["decay_rate"]["F64_per_step"],
+                                    "definition": errs["decay_rate"]["definition"]},
+                "taylor_green_2d": errs["small_taylor_green_2d"]}
     cpu = None
     if rank == 0:
         cpu = oracle_baseline(w, args.bulk, seconds=args.cpu_seconds)
@@ -725,15 +737,19 @@ def accuracy_gates(torch, lbm, dev, w, args, rho, u):
     D, dims, ncell = w["D"], w["dims"], int(np.prod(w["dims"]))
     n = dims[0]
     steps_i = int(round(4 * n / (2 * math.pi * w["u0"])))
+    from paper_2303_08163_gb300 import fits
     out = {"pointwise": {"steps": steps_i}, "curves": {}}
-    vel = {}
+    vel, rate = {}, {}
     for prec in (0, 1, 2):
         lat = lbm.Lattice(lbm.D3Q27, dims, w["tau"], w["eq"], 0, prec)
         lat.init_fields(rho, u, dtype=np.float32)
+        lat.set_option(lbm.OPT_DIAG_EVERY, 10)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         lat.step(steps_i)
         e1.record()
+        hist = lat.diag_history()
+        rate[prec] = fits.energy_decay_rate([h["step"] for h in hist], [h["kinetic"] for h in hist])
         r = torch.empty(ncell, device=dev, dtype=torch.float64)
         v = torch.empty(3, ncell, device=dev, dtype=torch.float64)
         lat.moments(dtype=np.float64, out=(r, v))
@@ -746,6 +762,9 @@ def accuracy_gates(torch, lbm, dev, w, args, rho, u):
     ref = torch.linalg.norm(vel[0])
     for prec in (1, 2):
         out["pointwise"][PREC_NAME[prec] + "_rel_l2_vs_F64"] = float(torch.linalg.norm(vel[prec] - vel[0]) / ref)
+        # slope of -ln E over the same window (E every 10 steps), relative to FP64
+        out["pointwise"][PREC_NAME[prec] + "_decay_rate_error_vs_F64"] = abs(rate[prec] / rate[0] - 1)
+    out["pointwise"]["F64_decay_rate_per_step"] = rate[0]
     del vel
     torch.cuda.empty_cache()
     every = 100

@@ -192,6 +192,43 @@ def test_lattice_over_2_31_cells(shape):
     torch.cuda.empty_cache()
 
 
+def test_tune_lattice_larger_than_half_of_hbm():
+    """The tuner needs no copy of the state: a binary16 D3Q27 lattice holding more than half
+    of the device's memory (1400^3 cells, about 148 GB, on a 284 GB GB300) is tuned in
+    place (the candidates run on a proxy of at most 2 GiB); the tuned TMA step then
+    matches the oracle on sampled cells after 1 and 2 steps."""
+    import torch
+    from paper_2303_08163_gb300 import lbm
+    total = torch.cuda.get_device_properties(0).total_memory
+    n = 8
+    while n ** 3 * 27 * 2 <= 0.52 * total:
+        n += 8
+    u0 = 0.1
+    tau = 0.5 + 3 * u0 * (n / (2 * math.pi)) / 1600.0
+    dims = (n, n, n)
+    lat = lbm.Lattice(lbm.D3Q27, dims, tau, lbm.ENTROPIC, 0, lbm.F16S)
+    state = lat.launch_info()["storage_bytes"]
+    assert state > total / 2
+    rho, u = inputs.taylor_green_3d_torch(n, u0=u0, device="cuda")
+    lat.init_fields(rho, u, dtype=np.float32)
+    del rho, u
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    assert free < state  # a full copy of the state would not fit
+    lat.set_option(lbm.OPT_TUNE, 1)
+    info = lat.launch_info()
+    print(f"{n}^3: state {state / 1e9:.1f} GB of {total / 1e9:.1f} GB, tuned shape {info}")
+    assert info["kernel"] == lbm.KERNEL_TMA and lat.step_count == 0
+    rho_fn, u_fn = inputs.taylor_green_3d_fields(n, u0=u0)
+    cells = sample_cells(dims, 24, seed=14)
+    lat.step(1)
+    check_sampled(lat, 3, dims, core.EQ_ENTROPIC, 0, tau, 2, rho_fn, u_fn, 1, cells, u0)
+    lat.step(1)
+    check_sampled(lat, 3, dims, core.EQ_ENTROPIC, 0, tau, 2, rho_fn, u_fn, 2, cells, u0)
+    lat.close()
+    torch.cuda.empty_cache()
+
+
 @pytest.mark.parametrize("prec", [2, 1])
 def test_turbulence_1024x512x512_sampled(prec):
     """The decaying-turbulence box at full size (1024 x 512 x 512, tau - 1/2 = 1e-4, the
