@@ -183,16 +183,18 @@ cudaError_t launch_one(lbm_ctx *c, int odd, int diag, cudaStream_t s) {
     return step_generic(a, c->gen_blocks, c->gen_threads, s);
 }
 
-// Default TMA shape: whole rows (several per job when short) if a row fits a direction
-// buffer, else aligned segments; stage count from the shared-memory budget.
+// Default TMA shape, used until the tuner runs: the shape the tuner picks on the large
+// workloads measured so far.  128 colliding threads; direction buffers of 2048 bytes for
+// D3Q27 (4096 when a row is longer, up to 4096 bytes) and 4096 bytes for D2Q9; whole rows
+// filling the buffer when a row fits, otherwise aligned segments; 2 stages for D3Q27 (two
+// blocks per SM) and 3 for D2Q9; as many blocks as fit on the device.
 bool default_tma_shape(lbm_ctx *c, TmaShape &t) {
     const int es = esize_of(c->prec);
     const int64_t rowb = c->lat.nx * (int64_t)es;
     const int U = 16 / es;
-    t.threads = 256;
-    const int capmax = c->D == 3 ? 2048 : 8192;
-    int cap = 1024;
-    while (cap < rowb && cap < capmax) cap *= 2;
+    t.threads = 128;
+    int cap = c->D == 3 ? 2048 : 4096;
+    if (c->D == 3 && rowb > cap && rowb <= 4096) cap = 4096;
     t.cap = cap;
     if (rowb <= cap) {
         t.seg = c->lat.nx;
@@ -201,8 +203,7 @@ bool default_tma_shape(lbm_ctx *c, TmaShape &t) {
         t.seg = (cap / es - 2 * U) / U * U;
         t.rows = 1;
     }
-    const int stage = c->Q * cap;
-    t.stages = std::max(2, std::min(kTmaMaxStages, (110 * 1024) / stage));
+    t.stages = c->D == 3 ? 2 : 3;
     t.smem_bytes = tma_smem_bytes(c->lat, t);
     if (t.smem_bytes < 0) return false;
     const int nb = tma_max_blocks_per_sm(c->lat, c->eq, c->bulk, t);
