@@ -101,27 +101,29 @@ D3Q27_1000 = [
 
 @pytest.mark.parametrize("name,dims,field,tau,shapes", D3Q27_1000, ids=[c[0] for c in D3Q27_1000])
 @pytest.mark.parametrize("bulk", [0, 1])
-def test_d3q27_fp64_1000_steps(name, dims, field, tau, shapes, bulk):
-    """D3Q27, entropic equilibrium (Eq. eq:Entropic_isothermal_EDF), bulk correction off
-    and on (Eq. eq:redefined_relaxation rate), FP64: after 1000 steps every population of
-    every kernel path equals the oracle's to 1e-12 (maximum relative error), and again one
-    step later (the other AA layout)."""
+@pytest.mark.parametrize("eq", [core.EQ_ENTROPIC, core.EQ_POLY2, core.EQ_PRODUCT])
+def test_d3q27_fp64_1000_steps(name, dims, field, tau, shapes, bulk, eq):
+    """D3Q27, FP64, each equilibrium (entropic Eq. eq:Entropic_isothermal_EDF, quadratic
+    Eq. eq:Poly2_isothermal_EDF, product form Eq. eq:Product_isothermal_EDF), bulk
+    correction off and on (Eq. eq:redefined_relaxation rate): after 1000 steps every
+    population of every kernel path equals the oracle's to 1e-12 (maximum relative
+    error), and again one step later (the other AA layout)."""
     import os
     lbm = lbm_mod()
     n = int(np.prod(dims))
     if field == "tgv":
         rho, u = inputs.taylor_green_3d(dims[0], u0=0.05)
     else:
-        rho, u = inputs.random_state(3, dims, seed=1000 + bulk, rho_range=(0.9, 1.1), u_max=0.1)
+        rho, u = inputs.random_state(3, dims, seed=1000 + bulk + 10 * eq, rho_range=(0.9, 1.1), u_max=0.1)
     assert rho.shape == (n,)
     core.set_threads(os.cpu_count() or 1)  # the same result bit for bit as one thread
     try:
-        ref = run_oracle(3, dims, core.EQ_ENTROPIC, bulk, tau, rho, u, 1000)
-        ref1 = core.step(3, dims, core.EQ_ENTROPIC, bulk, tau, 1, ref)
+        ref = run_oracle(3, dims, eq, bulk, tau, rho, u, 1000)
+        ref1 = core.step(3, dims, eq, bulk, tau, 1, ref)
     finally:
         core.set_threads(1)
     for shape in shapes:
-        lat = lbm.Lattice(lbm.D3Q27, dims, tau, lbm.ENTROPIC, bulk, lbm.F64)
+        lat = lbm.Lattice(lbm.D3Q27, dims, tau, eq, bulk, lbm.F64)
         lat.set_launch_shape(*shape)
         assert lat.launch_info()["kernel"] == shape[0]
         lat.init_fields(rho, u)
@@ -129,7 +131,7 @@ def test_d3q27_fp64_1000_steps(name, dims, field, tau, shapes, bulk):
         err = max_rel(lat.get_populations(), ref)
         lat.step(1)
         err1 = max_rel(lat.get_populations(), ref1)
-        print(f"{name} bulk={bulk} shape={shape}: max rel error {err:.2e} (1000 steps), {err1:.2e} (1001)")
+        print(f"{name} eq={eq} bulk={bulk} shape={shape}: max rel error {err:.2e} (1000 steps), {err1:.2e} (1001)")
         assert err <= 1e-12 and err1 <= 1e-12
         lat.close()
 
