@@ -33,7 +33,9 @@
  * dtype arguments: LBM_DT_F64 (double) or LBM_DT_F32 (float) for caller buffers;
  *   population calls also take LBM_DT_STORAGE (exact checkpoint of the stored values).
  * on_device: 0 = caller pointer is host memory (pageable or pinned), 1 = device memory
- *   on the context's device.
+ *   on the context's device.  Page-locked host buffers (cudaHostAlloc, cudaHostRegister)
+ *   of the field calls are read or written by the kernels directly across the CPU-GPU
+ *   link; pageable ones go through a device staging buffer.  The results are the same.
  * Ownership: the library owns its objects and all device memory it allocates; caller
  *   buffers are borrowed for the duration of the call only.
  * Streams: every call is ordered on the stream given at creation (NULL = legacy default

@@ -280,6 +280,19 @@ int stage_in(const void *src, size_t bytes, int on_device, cudaStream_t s, DevBu
     return LBM_OK;
 }
 
+// Device address of a page-locked host buffer (cudaHostAlloc or cudaHostRegister), or
+// nullptr for pageable or device memory.  Kernels read and write such a buffer directly
+// across the CPU-GPU link, as fast as a copy engine moves it, so the field upload and the
+// moment download need neither a staging buffer nor a separate copy pass.
+void *mapped_host(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 std::string tune_key(lbm_ctx *c) {
     cudaDeviceProp prop;
     int dev = 0;
@@ -705,7 +718,12 @@ int lbm_init_fields(lbm_ctx *c, const void *rho, const void *u, int dtype, int o
     if (!rho || !u || !valid_dtype(dtype)) return fail(LBM_EINVAL, "bad field arguments");
     const size_t es = dtype == LBM_DT_F64 ? 8 : 4;
     const void *dr = rho, *du = u;
-    if (!on_device) {
+    void *mr = on_device ? nullptr : mapped_host(rho), *mu = on_device ? nullptr : mapped_host(u);
+    if (mr && mu) {
+        // page-locked fields: the initialisation kernel reads them across the link
+        dr = mr;
+        du = mu;
+    } else if (!on_device) {
         void *pr, *pu;
         if ((rc = ctx_stage(c, 0, es * c->ncell, &pr))) return ctx_sticky(c, rc);
         if ((rc = ctx_stage(c, 1, es * c->ncell * c->D, &pu))) return ctx_sticky(c, rc);
@@ -786,15 +804,22 @@ int lbm_moments(lbm_ctx *c, void *rho, void *u, int dtype, int on_device) {
     if (!rho || !u || !valid_dtype(dtype)) return fail(LBM_EINVAL, "bad field arguments");
     const size_t es = dtype == LBM_DT_F64 ? 8 : 4;
     void *dr = rho, *du = u;
-    if (!on_device) {
+    void *mr = on_device ? nullptr : mapped_host(rho), *mu = on_device ? nullptr : mapped_host(u);
+    const bool direct = mr && mu;  // page-locked outputs: the kernel writes them across the link
+    if (direct) {
+        dr = mr;
+        du = mu;
+    } else if (!on_device) {
         if ((rc = ctx_stage(c, 0, es * c->ncell, &dr))) return ctx_sticky(c, rc);
         if ((rc = ctx_stage(c, 1, es * c->ncell * c->D, &du))) return ctx_sticky(c, rc);
     }
     cudaError_t e = moments(c->lat, c->rho0, (int)(c->step & 1), dr, du, dtype, c->stream);
     if (e != cudaSuccess) return ctx_sticky(c, cuda_fail("moments kernel", e));
     if (!on_device) {
-        CK(cudaMemcpyAsync(rho, dr, es * c->ncell, cudaMemcpyDeviceToHost, c->stream), "moments copy");
-        CK(cudaMemcpyAsync(u, du, es * c->ncell * c->D, cudaMemcpyDeviceToHost, c->stream), "moments copy");
+        if (!direct) {
+            CK(cudaMemcpyAsync(rho, dr, es * c->ncell, cudaMemcpyDeviceToHost, c->stream), "moments copy");
+            CK(cudaMemcpyAsync(u, du, es * c->ncell * c->D, cudaMemcpyDeviceToHost, c->stream), "moments copy");
+        }
         CK(cudaStreamSynchronize(c->stream), "moments sync");
         return read_status(c);
     }
@@ -1270,8 +1295,14 @@ int lbm_batch_init_fields(lbm_batch *b, const void *rho, const void *u, int dtyp
     if (!rho || !u || !valid_dtype(dtype)) return fail(LBM_EINVAL, "bad field arguments");
     const size_t es = dtype == LBM_DT_F64 ? 8 : 4;
     DevBuf dr, du;
-    if ((rc = stage_in(rho, es * b->total, on_device, b->stream, dr))) return batch_sticky(b, rc);
-    if ((rc = stage_in(u, es * b->total * b->D, on_device, b->stream, du))) return batch_sticky(b, rc);
+    void *mr = on_device ? nullptr : mapped_host(rho), *mu = on_device ? nullptr : mapped_host(u);
+    if (mr && mu) {  // page-locked fields: the kernel reads them across the link
+        dr.p = mr;
+        du.p = mu;
+    } else {
+        if ((rc = stage_in(rho, es * b->total, on_device, b->stream, dr))) return batch_sticky(b, rc);
+        if ((rc = stage_in(u, es * b->total * b->D, on_device, b->stream, du))) return batch_sticky(b, rc);
+    }
     cudaError_t e = batch_init(b->arena, b->d_cell_start, b->d_dims, b->count, b->D, b->eq, b->rho0, dr.p, du.p,
                                dtype, b->total, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(int32_t) * b->count, b->stream);
@@ -1422,7 +1453,12 @@ int lbm_batch_moments(lbm_batch *b, void *rho, void *u, int dtype, int on_device
     const size_t es = dtype == LBM_DT_F64 ? 8 : 4;
     void *dr = rho, *du = u;
     DevBuf br, bu;
-    if (!on_device) {
+    void *mr = on_device ? nullptr : mapped_host(rho), *mu = on_device ? nullptr : mapped_host(u);
+    const bool direct = mr && mu;  // page-locked outputs: the kernel writes them across the link
+    if (direct) {
+        dr = mr;
+        du = mu;
+    } else if (!on_device) {
         if (cudaMalloc(&br.p, es * b->total) != cudaSuccess || cudaMalloc(&bu.p, es * b->total * b->D) != cudaSuccess) {
             cudaGetLastError();
             return fail(LBM_ENOMEM, "moments staging");
@@ -1435,8 +1471,10 @@ int lbm_batch_moments(lbm_batch *b, void *rho, void *u, int dtype, int on_device
                                   dr, du, dtype, b->total, b->stream);
     if (e != cudaSuccess) return batch_sticky(b, cuda_fail("batch moments", e));
     if (!on_device) {
-        CK(cudaMemcpyAsync(rho, dr, es * b->total, cudaMemcpyDeviceToHost, b->stream), "moments copy");
-        CK(cudaMemcpyAsync(u, du, es * b->total * b->D, cudaMemcpyDeviceToHost, b->stream), "moments copy");
+        if (!direct) {
+            CK(cudaMemcpyAsync(rho, dr, es * b->total, cudaMemcpyDeviceToHost, b->stream), "moments copy");
+            CK(cudaMemcpyAsync(u, du, es * b->total * b->D, cudaMemcpyDeviceToHost, b->stream), "moments copy");
+        }
         CK(cudaStreamSynchronize(b->stream), "moments sync");
     }
     return LBM_OK;

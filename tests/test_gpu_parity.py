@@ -212,6 +212,69 @@ def test_reduced_precision_tma_shapes(D, dims, shape, prec, eq, bulk):
         lat.close()
 
 
+@pytest.mark.parametrize("prec", [0, 2])
+def test_host_buffers_pinned_pageable_device_agree(prec):
+    """lbm_init_fields and lbm_moments with page-locked host buffers (read and written by
+    the kernels across the link), pageable host buffers (staged) and device buffers give the
+    same state and the same moments bit for bit, for a single lattice and for a batch."""
+    import torch
+    lbm = lbm_mod()
+    dims = (40, 12, 9)
+    n = int(np.prod(dims))
+    rho, u = inputs.random_state(3, dims, seed=71, u_max=0.1)
+    rho32, u32 = rho.astype(np.float32), u.astype(np.float32)
+    srcs = {"pageable": (rho32, u32),
+            "pinned": (torch.from_numpy(rho32).pin_memory(), torch.from_numpy(u32).pin_memory()),
+            "device": (torch.from_numpy(rho32).cuda(), torch.from_numpy(u32).cuda())}
+    states, moms = {}, {}
+    for name, (r, v) in srcs.items():
+        lat = lbm.Lattice(lbm.D3Q27, dims, 0.6, lbm.ENTROPIC, 1, prec)
+        lat.init_fields(r, v, dtype=np.float32)
+        lat.step(3)
+        states[name] = lat.get_populations("storage")
+        if name == "pageable":
+            moms[name] = lat.moments(dtype=np.float32)
+        else:
+            out = (torch.empty(n, dtype=torch.float32), torch.empty(3, n, dtype=torch.float32))
+            if name == "pinned":
+                out = tuple(t.pin_memory() for t in out)
+            else:
+                out = tuple(t.cuda() for t in out)
+            lat.moments(dtype=np.float32, out=out)
+            torch.cuda.synchronize()
+            moms[name] = tuple(t.cpu().numpy() for t in out)
+        lat.close()
+    for name in ("pinned", "device"):
+        assert np.array_equal(states[name].view(np.uint8), states["pageable"].view(np.uint8)), name
+        for a, b in zip(moms[name], moms["pageable"]):
+            assert np.array_equal(a.reshape(-1).view(np.uint32), b.reshape(-1).view(np.uint32)), name
+    # batch: pinned fields in and pinned moments out against pageable
+    table = inputs.linear_mode_batch(count=9, seed=3, nmin=5, nmax=30)
+    bd = np.stack([table["nx"], table["ny"], np.ones(9, dtype=np.int32)], axis=1)
+    fields = [inputs.linear_mode_fields(table, k) for k in range(9)]
+    br = np.concatenate([f[0] for f in fields])
+    bu = np.concatenate([f[1].reshape(-1) for f in fields])
+    res = {}
+    for name in ("pageable", "pinned"):
+        b = lbm.Batch(lbm.D2Q9, bd, table["tau"], lbm.ENTROPIC, 0)
+        if name == "pinned":
+            b.init_fields(torch.from_numpy(br).pin_memory(), torch.from_numpy(bu).pin_memory())
+        else:
+            b.init_fields(br, bu)
+        b.step(5)
+        if name == "pinned":
+            out = (torch.empty(len(br), dtype=torch.float64).pin_memory(),
+                   torch.empty(len(bu), dtype=torch.float64).pin_memory())
+            b.moments(out=out)
+            res[name] = (b.get_populations(), out[0].numpy().copy(), out[1].numpy().copy())
+        else:
+            r2, u2 = b.moments()
+            res[name] = (b.get_populations(), r2, u2)
+        b.close()
+    for a, c in zip(res["pinned"], res["pageable"]):
+        assert np.array_equal(a.view(np.uint64), c.view(np.uint64))
+
+
 def test_init_and_moments_fp64():
     """f = f^eq(rho, u) at t = 0 and the exported moments match the oracle."""
     lbm = lbm_mod()
