@@ -5,8 +5,8 @@ autotuned one), on outputs the oracle can compute one by one:
   sampled cells after 1 and 2 steps (the oracle evaluates a (2n+1)^3 patch around each
   cell), and global mass / momentum over 40 steps.
 - D2Q9 4096^2 double shear layer, FP32: sampled cells after 1 and 2 steps.
-- 4096 batched D2Q9 instances (FP64): probe series and final populations of sampled
-  instances equal the oracle's to 1e-12.
+- 4096 batched D2Q9 instances (FP64) in the batch tuner's launch shape: probe series and
+  final populations of sampled instances equal the oracle's to 1e-12.
 - D3Q27 1024 x 512 x 512 decaying turbulence, binary16 and FP32: sampled cells after 1 and
   2 steps.
 - The largest lattice: 1304^3 cells (more than 2^31), binary16, both step kernels.
@@ -17,10 +17,12 @@ autotuned one), on outputs the oracle can compute one by one:
   which lies inside the rounding bound; on this field it changes it by about
   w_i |delta rho + 3 delta u|, far outside (tests/test_fullsize_power.py shows both on the
   CPU with the oracle).
-- The autotuned TMA kernel against the one-cell kernel at 512^3 (binary16 and FP32) and on
-  the 1024 x 512 x 512 turbulence box (binary16): the stored states after 1, 2 and 3 steps
-  are identical bit for bit (both kernels evaluate the same collision on the same stored
-  values, so any data-movement error shows up as a difference).
+- The autotuned TMA kernel against the one-cell kernel at 512^3 (binary16 and FP32), on
+  the 1024 x 512 x 512 turbulence box (binary16) and on the 4096^2 D2Q9 shear layer (FP32
+  in segments with halos, binary16 in whole 8 KB rows with the paired bodies): the stored
+  states after 1, 2 and 3 steps are identical bit for bit (both kernels evaluate the same
+  collision on the same stored values, so any data-movement error shows up as a
+  difference).
 
 The rounding bound of the sampled checks is derived in tests/fullsize_bounds.py.
 """
@@ -141,6 +143,8 @@ def test_batch_4096_sampled_instances():
     b = lbm.Batch(lbm.D2Q9, dims, table["tau"], core.EQ_ENTROPIC, 0)
     b.init_fields(rho, u)
     b.set_probe(kvec, 10)
+    b.autotune(steps=4)  # the benchmark's launch shape
+    print(f"batch tuned shape {b.launch_info()}")
     steps = 61
     b.step(steps)
     series = b.probe_series()
@@ -268,7 +272,8 @@ def test_turbulence_1024x512x512_sampled(prec):
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("case,prec", [("tgv512", 2), ("tgv512", 1), ("turb", 2)])
+@pytest.mark.parametrize("case,prec", [("tgv512", 2), ("tgv512", 1), ("turb", 2), ("shear4096", 1),
+                                       ("shear4096", 2)])
 def test_fullsize_tma_equals_one_cell_bitwise(case, prec):
     """At the full benchmark sizes and in the autotuned launch shape (whatever it is on
     this device: rows per job, segments, stages, threads, the paired binary16 body), the
@@ -278,20 +283,30 @@ def test_fullsize_tma_equals_one_cell_bitwise(case, prec):
     must also leave the state it was called on untouched."""
     import torch
     from paper_2303_08163_gb300 import lbm
+    lattice = lbm.D3Q27
     if case == "tgv512":
         n, u0 = 512, 0.1
         dims = (n, n, n)
         tau = 0.5 + 3 * u0 * (n / (2 * math.pi)) / 1600.0
         rho, u = inputs.taylor_green_3d_torch(n, u0=u0, device="cuda")
+    elif case == "shear4096":
+        # the double shear layer: FP32 rows of 16 KB run as segments with halos, binary16
+        # rows of 8 KB whole, with up to 512 threads and the paired D2Q9 bodies
+        lattice = lbm.D2Q9
+        dims = (4096, 4096, 1)
+        tau = 0.5 + 3e-5
+        r_np, u_np = inputs.double_shear_layer(4096, dtype=np.float32)
+        rho, u = torch.from_numpy(r_np).cuda(), torch.from_numpy(np.ascontiguousarray(u_np)).cuda()
     else:
         dims = (1024, 512, 512)
         tau = 0.5 + 1e-4
         rho, u = inputs.random_solenoidal_torch(dims, u_rms=0.05, device="cuda")
     ncell = int(np.prod(dims))
+    Q = 27 if lattice == lbm.D3Q27 else 9
     store = {1: torch.int32, 2: torch.int16}[prec]
-    a = lbm.Lattice(lbm.D3Q27, dims, tau, lbm.ENTROPIC, 0, prec)
+    a = lbm.Lattice(lattice, dims, tau, lbm.ENTROPIC, 0, prec)
     a.init_fields(rho, u, dtype=np.float32)
-    before = torch.empty(27 * ncell, dtype=store, device="cuda")
+    before = torch.empty(Q * ncell, dtype=store, device="cuda")
     a.get_populations("storage", out=before)
     a.set_option(lbm.OPT_TUNE, 1)  # the benchmark's launch shape
     after = torch.empty_like(before)
@@ -302,7 +317,7 @@ def test_fullsize_tma_equals_one_cell_bitwise(case, prec):
     info = a.launch_info()
     print(f"{case} prec={prec}: tuned shape {info}")
     assert info["kernel"] == lbm.KERNEL_TMA
-    b = lbm.Lattice(lbm.D3Q27, dims, tau, lbm.ENTROPIC, 0, prec)
+    b = lbm.Lattice(lattice, dims, tau, lbm.ENTROPIC, 0, prec)
     b.set_launch_shape(lbm.KERNEL_GENERIC, 256)
     b.init_fields(rho, u, dtype=np.float32)
     del rho, u
