@@ -242,15 +242,16 @@ def traffic_records():
         return []
 
 
-def ncu_traffic(kernel, workload_name, units, launch=None):
+def ncu_traffic(kernel, workload_name, units, launch=None, precision=None):
     """DRAM bytes per launch from the committed ncu records, scaled to `units` (cells, or
     cell updates for the batch) and the reason when there is none.  A record counts only
     for the kernel source it was taken on (the step-kernel source hash) and, for the
     single-lattice kernels, for the exact launch shape that ran (threads, blocks, stages,
     rows, segment, shared memory): another shape moves other bytes."""
-    recs = [r for r in traffic_records() if r.get("kernel") == kernel and r.get("workload") == workload_name]
+    recs = [r for r in traffic_records() if r.get("kernel") == kernel and r.get("workload") == workload_name
+            and (precision is None or r.get("precision") == precision)]
     if not recs:
-        return None, "no ncu record for this kernel and workload"
+        return None, "no ncu record for this kernel, workload and storage precision"
     recs = [r for r in recs if r.get("source_hash") == source_hash()]
     if not recs:
         return None, "the kernel source changed since the ncu records were taken"
@@ -260,6 +261,24 @@ def ncu_traffic(kernel, workload_name, units, launch=None):
             shape = {k: launch.get(k) for k in LAUNCH_KEYS}
             return None, f"no ncu record for the launch shape that ran {shape}"
     return recs[0]["dram_bytes_per_cell"] * units, recs[0].get("captured_on")
+
+
+def fp64_pipe(workload_name, bulk, launch, glups, sm_mhz):
+    """FP64-pipe instruction roofline of an FP64-storage run from the committed ncu record of
+    the same kernel source, workload, bulk setting and launch kind: executed FP64 thread
+    instructions per cell update x GLUPS against the pipe's 2 instructions per SM per
+    cycle (DADD, DMUL and DFMA alike).  None when no such record exists."""
+    kname = "k_step_tma" if launch.get("kernel") == 2 else "k_step_generic"
+    for r in traffic_records():
+        if (r.get("kernel") == kname and r.get("workload") == workload_name and r.get("precision") == "F64"
+                and r.get("bulk_corr") == bulk and r.get("source_hash") == source_hash()
+                and r.get("launch", {}).get("threads") == launch.get("threads")
+                and r.get("fp64_thread_inst_per_cell")):
+            ipc = r["fp64_thread_inst_per_cell"]
+            peak = 152 * 2 * (sm_mhz or 2070.0) / 1e3
+            return {"fp64_thread_inst_per_cell_update": ipc, "achieved_ginst_s": ipc * glups,
+                    "peak_ginst_s": peak, "frac": ipc * glups / peak, "source": r.get("captured_on")}
+    return None
 
 
 def aggregate(world, cells_per_rank, steps, rank_ms):
@@ -574,7 +593,7 @@ def run_native(args):
     achieved = algo_bytes / (launch_ms * 1e-3) / 1e9
     info = lat.launch_info()
     kname = "k_step_tma" if info["kernel"] == 2 else "k_step_generic"
-    traffic, traffic_note = ncu_traffic(kname, w["name"], ncell, launch=info)
+    traffic, traffic_note = ncu_traffic(kname, w["name"], ncell, launch=info, precision=PREC_NAME[prec])
     glups = aggregate(ws, ncell, args.steps, [t_max])
     # end to end through the C ABI with pinned host buffers
     rho_h = rho.cpu().pin_memory()
@@ -835,7 +854,8 @@ def compare_precisions(torch, lbm, dev, w, args, rho, u, sm_mhz=None):
                 peak64 = fp64_peak_gflops(sm_mhz)
                 out[key]["roofline"] = {"bound": "alu", "flops_per_cell_update": fpc,
                                         "achieved": fpc * glups, "peak": peak64,
-                                        "unit": "GFLOP/s (FP64)", "frac": fpc * glups / peak64}
+                                        "unit": "GFLOP/s (FP64)", "frac": fpc * glups / peak64,
+                                        "fp64_pipe": fp64_pipe(w["name"], bulk, out[key]["launch"], glups, sm_mhz)}
             lat.close()
             torch.cuda.empty_cache()
     return out
@@ -999,7 +1019,7 @@ def run_batch(args, w, torch, lbm, dev, rank, ws):
            and all(r.get("launch", {}).get(k) == launch[k] for k in ("threads", "blocks"))]
     traffic = rec[0]["dram_bytes_per_cell"] * total * args.steps if rec else None
     pipe = None
-    if rec and rec[0].get("fp64_thread_inst_per_cell"):
+    if rec and rec[0].get("fp64_thread_inst_per_cell") and rec[0].get("bulk_corr", 0) == args.bulk:
         # the FP64 pipe issues 2 thread instructions per SM per cycle (DADD, DMUL and DFMA
         # alike), so its roofline counts instructions, not flops
         ipc = rec[0]["fp64_thread_inst_per_cell"]

@@ -31,9 +31,10 @@ def test_traffic_records_match_the_sources_and_workloads():
         assert r["source_hash"] == bench.source_hash(), "kernel sources changed since the capture"
         # every record names the launch shape it was taken in
         keys = ("threads", "blocks") if r["kernel"] == "k_step_batch" else bench.LAUNCH_KEYS
+        assert r["precision"] in ("F64", "F32", "F16S") and r["bulk_corr"] in (0, 1)
         assert all(isinstance(r["launch"].get(k), int) for k in keys), r
     w = bench.workload(Args("tgv3d"))
-    tgv = [r for r in recs if r["workload"] == w["name"]]
+    tgv = [r for r in recs if r["workload"] == w["name"] and r["kernel"] == "k_step_tma" and r["precision"] == "F16S"]
     assert tgv
     for r in tgv:
         per_cell, note = bench.ncu_traffic("k_step_tma", w["name"], 1, launch=r["launch"])
@@ -95,3 +96,12 @@ def test_defaults_are_the_contract():
 def test_aggregate_is_weak_scaling(world):
     g = bench.aggregate(world, 1000, 10, [2.0] * world)
     assert abs(g - world * 1000 * 10 / 2e-3 / 1e9) < 1e-12
+
+
+def test_fp64_pipe_record_of_the_fp64_storage_path():
+    w = bench.workload(Args("tgv3d"))
+    launch = {"kernel": 1, "threads": 128, "blocks": 2432}
+    pipe = bench.fp64_pipe(w["name"], 0, launch, 2.44, 2070.0)
+    assert pipe is not None and 200 < pipe["fp64_thread_inst_per_cell_update"] < 300
+    assert 0.5 < pipe["frac"] < 1.05
+    assert bench.fp64_pipe(w["name"], 0, dict(launch, threads=256), 2.44, 2070.0) is None
