@@ -88,6 +88,66 @@ def test_taylor_green_64_fp64_1000_steps(kernel):
     lat.close()
 
 
+@pytest.mark.parametrize("eq", [core.EQ_POLY2, core.EQ_PRODUCT, core.EQ_ENTROPIC])
+def test_d2q9_fp64_1000_steps_bulk_all_equilibria(eq):
+    """D2Q9 64^2 Taylor-Green (u0 = 0.05, tau = 0.8), FP64, bulk correction on (Eq.
+    eq:redefined_relaxation rate), each equilibrium, TMA and one-cell paths, the TMA path
+    replayed from a CUDA graph: after 1000 and 1001 steps every population equals the
+    oracle's to 1e-12 (maximum relative error)."""
+    import os
+    lbm = lbm_mod()
+    n, tau = 64, 0.8
+    rho, u = inputs.taylor_green_2d(n, u0=0.05)
+    core.set_threads(os.cpu_count() or 1)  # the same result bit for bit as one thread
+    try:
+        ref = run_oracle(2, (n, n, 1), eq, 1, tau, rho, u, 1000)
+        ref1 = core.step(2, (n, n, 1), eq, 1, tau, 1, ref)
+    finally:
+        core.set_threads(1)
+    for shape, graph in (((lbm.KERNEL_TMA, 128, 3, 8, n, 4096), True), ((lbm.KERNEL_GENERIC, 128), False)):
+        lat = lbm.Lattice(lbm.D2Q9, (n, n, 1), tau, eq, 1, lbm.F64)
+        lat.set_launch_shape(*shape)
+        if graph:
+            lat.set_option(lbm.OPT_USE_GRAPH, 1)
+        lat.init_fields(rho, u)
+        lat.step(1000)
+        assert max_rel(lat.get_populations(), ref) <= 1e-12
+        lat.step(1)
+        assert max_rel(lat.get_populations(), ref1) <= 1e-12
+        lat.close()
+
+
+def test_batch_fp64_1000_steps():
+    """Batched D2Q9 instances (ragged sizes, per-instance tau, shear and acoustic waves on
+    background flows), entropic with the bulk correction, FP64: 1000 steps in three calls
+    (three persistent launches from CUDA graphs), probes every 50 steps; populations and
+    probe series equal the oracle's instance by instance to 1e-12."""
+    lbm = lbm_mod()
+    table = inputs.linear_mode_batch(count=10, seed=19, nmin=6, nmax=32)
+    count = len(table["nx"])
+    dims = np.stack([table["nx"], table["ny"], np.ones(count, dtype=np.int32)], axis=1)
+    fields = [inputs.linear_mode_fields(table, k) for k in range(count)]
+    rho = np.concatenate([f[0] for f in fields])
+    u = np.concatenate([f[1].reshape(-1) for f in fields])
+    kvec = np.stack([table["nmode"], np.zeros(count, np.int32), np.zeros(count, np.int32)], axis=1)
+    b = lbm.Batch(lbm.D2Q9, dims, table["tau"], core.EQ_ENTROPIC, 1)
+    b.init_fields(rho, u)
+    b.set_probe(kvec, 50)
+    for n in (333, 444, 223):
+        b.step(n)
+    assert b.info()["step"] == 1000
+    series, pops = b.probe_series(), b.get_populations()
+    assert np.all(b.status() == 0)
+    for k in range(count):
+        d3 = (int(dims[k, 0]), int(dims[k, 1]), 1)
+        f0 = core.init(2, d3, core.EQ_ENTROPIC, fields[k][0], fields[k][1])
+        fk, sk = core.run_probed(2, d3, core.EQ_ENTROPIC, 1, float(table["tau"][k]), 1000, 50, tuple(kvec[k]), f0)
+        c0, c1 = b.cell_start[k], b.cell_start[k + 1]
+        assert max_rel(pops[9 * c0: 9 * c1].reshape(9, -1), fk) <= 1e-12
+        assert np.all(np.abs(series[k] - sk) <= 1e-12 * np.abs(sk) + 1e-13 * int(c1 - c0))
+    b.close()
+
+
 # D3Q27 FP64 over 1000 steps: (name, dims, fields, tau, launch shapes).  The TMA shapes
 # cover several whole rows per job with a ragged last row group (y wrap) and aligned
 # row segments with halos; the one-cell kernel is the second path.
