@@ -50,7 +50,7 @@ __device__ __forceinline__ CellMoments<typename Storage<P>::R> aa_cell_step(
             f[i] = St::load(A[(int64_t)(Q - 1 - i) * plane + src]);
         }
     }
-    const CellMoments<R> m = collide<D, EQ, BULK, R>(f, rho0, omega0, six_nu);
+    const CellMoments<R> m = collide<D, EQ, BULK, R, relax_two_fma<D, P>()>(f, rho0, omega0, six_nu);
     if (!odd) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) A[(int64_t)(Q - 1 - i) * plane + cell] = St::store(f[i]);

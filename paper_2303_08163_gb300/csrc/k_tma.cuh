@@ -271,7 +271,7 @@ __device__ __forceinline__ void tma_compute(const lbmh::StepArgs &a, const TmaGe
         if (LBM_CHECK(p.row + min(p.xm, p.x) >= 0 && p.row + max(p.xp, p.x) < g.bufstride, a.status)) {
             R f[Q];
             tma_load_cell<D, P, CAPB>(st, p, a.odd, f);
-            const CellMoments<R> m = collide<D, EQ, BULK, R>(f, rho0, omega0, six_nu);
+            const CellMoments<R> m = collide<D, EQ, BULK, R, relax_two_fma<D, P>()>(f, rho0, omega0, six_nu);
             tma_store_cell<D, P, CAPB>(st, p, a.odd, f);
             if (a.diag) loc.add(m.rho, m.u, rho0);
         }
@@ -367,8 +367,8 @@ __device__ __forceinline__ void tma_compute_pairs(const lbmh::StepArgs &a, const
                     }
                 }
             }
-            const CellMoments<float> ma = collide<D, EQ, BULK, float>(fa, rho0, omega0, six_nu);
-            const CellMoments<float> mb = collide<D, EQ, BULK, float>(fb, rho0, omega0, six_nu);
+            const CellMoments<float> ma = collide<D, EQ, BULK, float, relax_two_fma<D, P_F16S>()>(fa, rho0, omega0, six_nu);
+            const CellMoments<float> mb = collide<D, EQ, BULK, float, relax_two_fma<D, P_F16S>()>(fb, rho0, omega0, six_nu);
             if (mode == 0) {
     #pragma unroll
                 for (int i = 0; i < Q; ++i) st_pair(row + (Q - 1 - i) * bs, xa, fa[i], fb[i]);

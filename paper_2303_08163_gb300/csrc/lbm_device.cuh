@@ -282,11 +282,19 @@ __host__ __device__ __forceinline__ CellMoments<R> moments_shifted(const R (&f)[
 }
 
 // The relaxation f* = (1 - 2beta) f + 2beta w_i (drho + rho h_i) of one direction of
-// weight class c.  FP64 (bound by the FP64 pipe): two FMAs per direction, with the
-// per-class products 2beta w rho and 2beta w drho formed once per cell; FP32: the factored
-// form 2beta w (rho h + drho) + (1 - 2beta) f (measured faster for FP32 storage and equal
-// for binary16, where the arithmetic hides under the memory traffic).
-template <typename R> struct Relax {
+// weight class c, in one of two forms.  TWO_FMA: two FMAs per direction, with the
+// per-class products 2beta w rho and 2beta w drho formed once per cell (fewest
+// instructions: used where instruction issue is the bound, FP64 and D2Q9 with binary16
+// storage).  Otherwise the factored form 2beta w (rho h + drho) + (1 - 2beta) f, which
+// measured faster for the bandwidth-bound FP32 and D3Q27 binary16 steps (fewer live
+// registers).  Both kernels of a lattice use the same form, so their states agree bit for
+// bit.
+template <int D, int P>
+__host__ __device__ constexpr bool relax_two_fma() {
+    return P == P_F64 || (D == 2 && P == P_F16S);
+}
+
+template <typename R, bool TWO_FMA = (sizeof(R) == 8)> struct Relax {
     R keep, rho, drho, omw[4], wr[4], wd[4];
     __host__ __device__ __forceinline__ Relax(R om, double w0, double w1, double w2, double w3, R rho_,
                                               R drho_)
@@ -300,7 +308,7 @@ template <typename R> struct Relax {
         }
     }
     __host__ __device__ __forceinline__ R operator()(int c, R h, R f) const {
-        if constexpr (sizeof(R) == 8) return fma_r(wr[c], h, fma_r(keep, f, wd[c]));
+        if constexpr (TWO_FMA) return fma_r(wr[c], h, fma_r(keep, f, wd[c]));
         else return fma_r(omw[c], fma_r(rho, h, drho), keep * f);
     }
 };
@@ -353,7 +361,7 @@ __host__ __device__ __forceinline__ void entropic_factors_one_division(
 // pre-collision moments (the macroscopic state at the current time step).  The
 // equilibrium term h_i of each direction is formed inside the relaxation loop from the
 // per-axis factors, so only the Q populations and O(D^2) factors stay live.
-template <int D, int EQ, bool BULK, typename R>
+template <int D, int EQ, bool BULK, typename R, bool TWO_FMA = (sizeof(R) == 8)>
 __host__ __device__ __forceinline__ CellMoments<R> collide(R (&f)[qof(D)], R rho0, R omega0, R six_nu) {
     constexpr int Q = qof(D);
     // weights per number of nonzero velocity components, folded at compile time
@@ -375,7 +383,7 @@ __host__ __device__ __forceinline__ CellMoments<R> collide(R (&f)[qof(D)], R rho
         if constexpr (D == 3) k = fmax(k, m.u[2] * m.u[2]);
         const R om = collision_rate<EQ, BULK, R>(k, omega0, six_nu);
         const R mh = R(-1.5) * uu;
-        const Relax<R> relax(om, kW0, kW1, kW2, kW3, m.rho, drho);
+        const Relax<R, TWO_FMA> relax(om, kW0, kW1, kW2, kW3, m.rho, drho);
         const R upm = m.u[0] + m.u[1], umm = m.u[0] - m.u[1];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -395,7 +403,7 @@ __host__ __device__ __forceinline__ CellMoments<R> collide(R (&f)[qof(D)], R rho
         R kmax = fmax(key[0], key[1]);
         if constexpr (D == 3) kmax = fmax(kmax, key[2]);
         const R om = collision_rate<EQ, BULK, R>(kmax, omega0, six_nu);
-        const Relax<R> relax(om, kW0, kW1, kW2, kW3, m.rho, drho);
+        const Relax<R, TWO_FMA> relax(om, kW0, kW1, kW2, kW3, m.rho, drho);
         const R dx[3] = {dm[0], d0[0], dp[0]};
         const R dy[3] = {dm[1], d0[1], dp[1]};
         const R tx[3] = {R(1) + dm[0], R(1) + d0[0], R(1) + dp[0]};
