@@ -749,6 +749,50 @@ def test_batch_autotune_keeps_state_and_parity():
 
 # ------------------------------------------------------------------- degenerate states
 
+TINY = [(2, (1, 1, 1)), (2, (1, 5, 1)), (2, (3, 1, 1)), (2, (2, 2, 1)), (3, (1, 1, 1)), (3, (2, 1, 3)),
+        (3, (1, 4, 1))]
+
+
+@pytest.mark.parametrize("D,dims", TINY)
+@pytest.mark.parametrize("eq", [core.EQ_ENTROPIC, core.EQ_POLY2, core.EQ_PRODUCT])
+def test_tiny_periodic_lattices_fp64(D, dims, eq):
+    """Lattices so small that a cell is its own neighbour along an axis (periodic wrap onto
+    itself) or has a single neighbour: FP64, bulk correction on, 57 steps, against the
+    oracle to 1e-12; the same lattices as instances of one batch."""
+    lbm = lbm_mod()
+    rho, u = inputs.random_state(D, dims, seed=900 + 3 * eq + D, u_max=0.1)
+    tau = 0.58
+    got, _ = run_gpu(D, dims, eq, 1, tau, 0, rho, u, 57)
+    ref = run_oracle(D, dims, eq, 1, tau, rho, u, 57)
+    assert max_rel(got, ref) <= 1e-12
+
+
+def test_tiny_instances_in_a_batch():
+    """A batch of degenerate instances (1 x 1, 1 x 7, 2 x 1, 3 x 3 cells) beside a larger one:
+    populations and probe series after 41 steps equal the oracle's instance by instance."""
+    lbm = lbm_mod()
+    dims = np.array([[1, 1, 1], [1, 7, 1], [2, 1, 1], [3, 3, 1], [16, 9, 1]], dtype=np.int32)
+    count = len(dims)
+    taus = np.array([0.6, 0.75, 0.52, 1.3, 0.9])
+    states = [inputs.random_state(2, tuple(int(v) for v in d), seed=60 + k, u_max=0.1) for k, d in enumerate(dims)]
+    rho = np.concatenate([st[0] for st in states])
+    u = np.concatenate([st[1].reshape(-1) for st in states])
+    kvec = np.array([[0, 0, 0], [0, 1, 0], [1, 0, 0], [1, 1, 0], [2, 1, 0]], dtype=np.int32)
+    b = lbm.Batch(lbm.D2Q9, dims, taus, core.EQ_ENTROPIC, 1)
+    b.init_fields(rho, u)
+    b.set_probe(kvec, 4)
+    b.step(41)
+    series, pops = b.probe_series(), b.get_populations()
+    assert np.all(b.status() == 0)
+    for k in range(count):
+        d3 = tuple(int(v) for v in dims[k])
+        f0 = core.init(2, d3, core.EQ_ENTROPIC, states[k][0], states[k][1])
+        fk, sk = core.run_probed(2, d3, core.EQ_ENTROPIC, 1, float(taus[k]), 41, 4, tuple(kvec[k]), f0)
+        c0, c1 = b.cell_start[k], b.cell_start[k + 1]
+        assert max_rel(pops[9 * c0: 9 * c1].reshape(9, -1), fk) <= 1e-12
+        assert np.all(np.abs(series[k] - sk) <= 1e-12 * np.abs(sk) + 1e-13 * int(c1 - c0))
+    b.close()
+
 @pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("shape", [(1, 128), (2, 128, 2, 2, 16, 1024)])
 def test_rest_state_is_a_fixed_point(prec, shape):
